@@ -1,0 +1,223 @@
+/*
+ * polar_express.h -- C ABI of the GB300 (sm_103a) Polar Express library.
+ *
+ * The library computes the polar factor polar(G) = U V^T of G = U S V^T
+ * (Eq. matrixsign) with the Polar Express method: Frobenius normalisation
+ * followed by T odd polynomial steps X <- a_t X + (b_t A + c_t A^2) X with
+ * A = X X^T on the short side (Alg. 1, online stage; Sec. 3.5 Horner form).
+ * The per-step coefficients come from the greedy minimax construction of
+ * Thm. 1 (Alg. 1, offline stage), solved on the host in FP64.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: a pe_status. On any status other than PE_OK a thread-local
+ *    message is available from pe_last_error().
+ *  - Argument errors (PE_EINVAL, PE_EUNSUPPORTED) are detected synchronously,
+ *    before anything is enqueued; device buffers are then left untouched.
+ *  - Device entry points are asynchronous with respect to the host: they
+ *    enqueue work on `stream` (a cudaStream_t passed as void*; NULL is the
+ *    legacy default stream) and return. Failures that only the device can
+ *    see (a bounded wait that expired, a non-finite norm) are latched in a
+ *    per-device status word and reported by pe_sync_status() and by the next
+ *    device call, as PE_ETIMEOUT or PE_ECUDA.
+ *  - Matrices are dense row-major: element (i, j) of an m x n matrix with
+ *    leading dimension ld lives at base[i * ld + j].
+ *  - Workspace is owned by the library: a per-device pool that grows on
+ *    demand (cudaMalloc, never inside a stream capture) and is freed by
+ *    pe_release(). Calls that would allocate while `stream` is capturing
+ *    fail with PE_EINVAL; warm the call up once before capturing it.
+ *  - Calls that share workspace are serialised by the library's host lock;
+ *    concurrent calls on different streams of one device therefore also
+ *    serialise their enqueue, and their kernels must not overlap on the
+ *    device (keep them on one stream or order the streams).
+ */
+#ifndef POLAR_EXPRESS_H
+#define POLAR_EXPRESS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PE_OK = 0,
+    PE_EINVAL = 1,        /* bad argument */
+    PE_ENOMEM = 2,        /* workspace allocation failed */
+    PE_ECUDA = 3,         /* a CUDA runtime/driver call failed, or a non-finite norm */
+    PE_ENOCONV = 4,       /* the Remez iteration hit its iteration cap */
+    PE_ETIMEOUT = 5,      /* a bounded device wait expired (results invalid) */
+    PE_EUNSUPPORTED = 6   /* valid request this build or device cannot run */
+} pe_status;
+
+/* Arithmetic of the online stage. */
+typedef enum {
+    PE_FP32 = 0,   /* plain method: FP32 operands, FP32 FMA accumulation (no TF32) */
+    PE_BF16 = 1,   /* BF16 tensor-core operands, FP32 accumulation, FP32 master X */
+    PE_BF16X3 = 2  /* split BF16: x = hi + lo, three BF16 products per k-step
+                      (hi*hi + hi*lo + lo*hi), FP32 accumulation */
+} pe_dtype;
+
+/* Element type of the caller's matrices. */
+typedef enum {
+    PE_IO_FP32 = 0,
+    PE_IO_BF16 = 1
+} pe_io_type;
+
+/* Flags for pe_coeffs_ex. */
+#define PE_SAFETY_SKIP_LAST 1u  /* leave the final row without the safety factor
+                                   (App. G: it may be omitted in the last step) */
+
+/* Library version as 10000*major + 100*minor + patch. */
+int pe_version(void);
+
+/*
+ * pe_coeffs -- offline stage: the greedy minimax coefficient table.
+ *
+ * Defined by Thm. 1 (Eq. greedy, Eq. newbounds) with the stabilisations of
+ * Sec. 3.4 / App. G and the offline code of App. A:
+ *   l_1 = l, u_1 = 1; for t = 1..T:
+ *     p_t = minimax odd polynomial of `degree` for x -> 1 on
+ *           [max(l_t, kappa u_t), u_t]  (degree 5: Remez of Alg. 3, App. F;
+ *           degree 3: closed form Eq. deg3_solution);
+ *     p_t <- p_t * 2 / (p_t(l_t) + max p_t on [l_t, u_t])   (recentring);
+ *     l_{t+1} = p_t(l_t), u_{t+1} = 2 - l_{t+1};
+ *   then every row that did not come from the l/u -> 1 shortcut (App. F) is
+ *   replaced by p_t(x / safety).
+ * kappa = 0.02407327424182761 for degree 5 (App. A), 0.1 for degree 3
+ * (Alg. 1's u/10).
+ *
+ *   degree  3 or 5.
+ *   l       lower bound on the normalised singular values, 0 < l <= 1.
+ *   T       number of steps, 1 <= T <= 64.
+ *   safety  >= 1; 1 disables the safety factor (the paper uses 1.01).
+ *   coeffs  out, host, caller-owned, 3*T doubles: row t is (a_t, b_t, c_t) of
+ *           p_t(x) = a_t x + b_t x^3 + c_t x^5 (c_t = 0 for degree 3).
+ *   bounds  out, host, caller-owned, 2*(T+1) doubles (l_t, u_t) before the
+ *           safety factor, or NULL.
+ * Pure host FP64 code, deterministic and reproducible bit for bit (no FMA
+ * contraction; fixed elimination order in the 4x4 solves).
+ * Errors: PE_EINVAL for arguments out of range or NULL coeffs, PE_ENOCONV if
+ * a Remez solve does not converge in 100 iterations.
+ */
+int pe_coeffs(int degree, double l, int T, double safety, double* coeffs, double* bounds);
+
+/*
+ * pe_coeffs_ex -- pe_coeffs with the remaining knobs of the offline stage.
+ *   cushion      kappa; a negative value selects the default for `degree`,
+ *                0 disables cushioning (the pure greedy optimum of Thm. 1).
+ *   flags        PE_SAFETY_SKIP_LAST or 0.
+ *   remez_iters  out, nullable: T ints, Remez iterations used per step
+ *                (0 for the shortcut and for degree 3).
+ */
+int pe_coeffs_ex(int degree, double l, int T, double safety, double cushion, unsigned flags,
+                 double* coeffs, double* bounds, int* remez_iters);
+
+/*
+ * pe_polar -- online stage for one matrix, in place.
+ *
+ * Computes X_T = p_T(...p_1(X_0)) with X_0 = G / (1.01 ||G||_F + 1e-7)
+ * (App. A online code) taken on the short side (transposed when m > n, so
+ * that A = X X^T is min(m,n) x min(m,n); App. A, Sec. H), and each step
+ * A = X X^T, B = b_t A + c_t A^2, X <- a_t X + B X (Sec. 3.5).
+ *
+ *   X       in/out, device, m x n row-major contiguous FP32 (ld = n). On
+ *           return (stream order) it holds X_T ~ polar(G).
+ *   m, n    >= 1.
+ *   table   host, T rows of (a, b, c) doubles (from pe_coeffs or any fixed
+ *           table such as Newton-Schulz (15/8, -10/8, 3/8)); cast to FP32.
+ *   T       1..64.
+ *   dtype   a pe_dtype.
+ *   stream  cudaStream_t as void*.
+ * Errors: PE_EINVAL (NULL pointers, sizes, T, dtype, non-finite table),
+ * PE_ENOMEM, PE_ECUDA, PE_EUNSUPPORTED (device is not sm_103).
+ */
+int pe_polar(void* X, int64_t m, int64_t n, const double* table, int T, int dtype, void* stream);
+
+/*
+ * pe_polar_ex -- pe_polar with explicit layout, element type and the
+ * normalisation constants.
+ *   ld          leading dimension in elements, >= n.
+ *   io_type     PE_IO_FP32 or PE_IO_BF16 (X is read and written in that type;
+ *               the iteration itself runs in `dtype`).
+ *   norm_scale  multiplies ||G||_F (App. A code: 1.01; Alg. 1: 1.0).
+ *   norm_eps    added to the scaled norm (App. A code: 1e-7; Alg. 1: 1e-2).
+ */
+int pe_polar_ex(void* X, int64_t m, int64_t n, int64_t ld, int io_type,
+                const double* table, int T, int dtype,
+                double norm_scale, double norm_eps, void* stream);
+
+/*
+ * pe_polar_batched -- online stage for a list of matrices of uneven shapes
+ * (all of a model's Muon parameters), in place.
+ *
+ * Same mathematics as pe_polar applied to each X[i] independently. The
+ * matrices are processed together: one grouped normalisation launch, then per
+ * polynomial step one persistent grouped launch (BF16 paths) that runs the
+ * Gram, A^2 and update tiles of every matrix with per-matrix readiness
+ * counters, all inside a CUDA graph cached by the library under the key
+ * (pointers, shapes, T, dtype, table). The first call with a new key tunes
+ * the tile schedule and captures the graph (it synchronises `stream` once);
+ * later calls replay the graph.
+ *
+ *   X       host array of `count` device pointers, each m[i] x n[i] row-major
+ *           contiguous FP32, in/out.
+ *   m, n    host arrays of `count` sizes (>= 1).
+ *   count   1..4096.
+ *   table, T, dtype, stream as for pe_polar.
+ * Errors: as pe_polar; a bounded readiness wait that expires on the device is
+ * reported as PE_ETIMEOUT by pe_sync_status() or the next call.
+ */
+int pe_polar_batched(void* const* X, const int64_t* m, const int64_t* n, int count,
+                     const double* table, int T, int dtype, void* stream);
+
+/*
+ * pe_polar_batched_ex -- pe_polar_batched with the element type and the
+ * normalisation constants of pe_polar_ex, and control over the plan:
+ *   flags  bit 0 (PE_BATCH_NO_GRAPH): enqueue kernels directly, no graph;
+ *          bit 1 (PE_BATCH_NO_TUNE): keep the default tile schedule;
+ *          bit 2 (PE_BATCH_PHASED): three grouped launches per step (Gram,
+ *          A^2, update) instead of one persistent launch.
+ */
+#define PE_BATCH_NO_GRAPH 1u
+#define PE_BATCH_NO_TUNE 2u
+#define PE_BATCH_PHASED 4u
+int pe_polar_batched_ex(void* const* X, const int64_t* m, const int64_t* n, int count, int io_type,
+                        const double* table, int T, int dtype,
+                        double norm_scale, double norm_eps, unsigned flags, void* stream);
+
+/*
+ * pe_sync_status -- synchronise `stream` and report (then clear) the device
+ * status word of the current device: PE_OK, PE_ETIMEOUT (a bounded wait
+ * expired), PE_ECUDA (a kernel error or a non-finite norm).
+ */
+int pe_sync_status(void* stream);
+
+/* Number of this library's kernels enqueued (directly or inside replayed
+ * graphs) on the calling process since load; for launch accounting. */
+int64_t pe_launch_count(void);
+
+/* Message for the last non-OK status returned on this thread ("" if none). */
+const char* pe_last_error(void);
+
+/* Free all workspace and cached plans of all devices. Safe to call anytime
+ * the library's work has completed. */
+void pe_release(void);
+
+/*
+ * pe_debug_set -- test hooks, off by default.
+ *   key 1: withhold the readiness signal of matrix `value` in the next
+ *          persistent grouped launch (value < 0 disables), so that its
+ *          consumers' bounded waits expire; the launch completes with
+ *          invalid results and PE_ETIMEOUT is latched.
+ *   key 2: wait limit of the persistent kernel in nanoseconds (0 = default).
+ *   key 3: make the next workspace allocation fail (value != 0).
+ * Returns PE_EINVAL for an unknown key.
+ */
+int pe_debug_set(int key, int64_t value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLAR_EXPRESS_H */

@@ -1,0 +1,217 @@
+"""Polar Express on GB300: Python binding of the C-ABI library.
+
+Argument marshalling only; every step of the online stage runs in the
+library's CUDA kernels. The names follow the C ABI (include/polar_express.h):
+
+* ``pe_coeffs(degree, l, T, safety)``: offline FP64 coefficient table
+  (Thm. 1 greedy minimax composition, Alg. 3 Remez, App. A stabilisations).
+* ``pe_polar(X, table, dtype)``: polar factor of one CUDA tensor, in place.
+* ``pe_polar_batched(Xs, table, dtype)``: a list of CUDA tensors of uneven
+  shapes, one persistent grouped launch per polynomial step in a cached
+  CUDA graph.
+
+PyTorch is used only for device memory and streams. If the shared library is
+missing the binding raises; it never falls back to another implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+PE_OK, PE_EINVAL, PE_ENOMEM, PE_ECUDA, PE_ENOCONV, PE_ETIMEOUT, PE_EUNSUPPORTED = range(7)
+PE_FP32, PE_BF16, PE_BF16X3 = 0, 1, 2
+PE_IO_FP32, PE_IO_BF16 = 0, 1
+PE_SAFETY_SKIP_LAST = 1
+PE_BATCH_NO_GRAPH, PE_BATCH_NO_TUNE, PE_BATCH_PHASED = 1, 2, 4
+
+DTYPES = {"fp32": PE_FP32, "bf16": PE_BF16, "bf16x3": PE_BF16X3}
+_STATUS = {0: "PE_OK", 1: "PE_EINVAL", 2: "PE_ENOMEM", 3: "PE_ECUDA", 4: "PE_ENOCONV",
+           5: "PE_ETIMEOUT", 6: "PE_EUNSUPPORTED"}
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "polar_express.h")
+
+
+class PolarExpressError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.library_path()
+
+
+def lib() -> ctypes.CDLL:
+    """Load the shared library (it must have been built with build())."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise PolarExpressError(PE_EUNSUPPORTED,
+                                f"{path} is missing; build it with paper_2505_16932_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    c_d, c_i, c_u, c_p, c_i64 = ctypes.c_double, ctypes.c_int, ctypes.c_uint, ctypes.c_void_p, ctypes.c_int64
+    P_d = ctypes.POINTER(c_d)
+    P_i = ctypes.POINTER(c_i)
+    P_i64 = ctypes.POINTER(c_i64)
+    sig = {
+        "pe_version": (c_i, []),
+        "pe_coeffs": (c_i, [c_i, c_d, c_i, c_d, P_d, P_d]),
+        "pe_coeffs_ex": (c_i, [c_i, c_d, c_i, c_d, c_d, c_u, P_d, P_d, P_i]),
+        "pe_polar": (c_i, [c_p, c_i64, c_i64, P_d, c_i, c_i, c_p]),
+        "pe_polar_ex": (c_i, [c_p, c_i64, c_i64, c_i64, c_i, P_d, c_i, c_i, c_d, c_d, c_p]),
+        "pe_polar_batched": (c_i, [ctypes.POINTER(c_p), P_i64, P_i64, c_i, P_d, c_i, c_i, c_p]),
+        "pe_polar_batched_ex": (c_i, [ctypes.POINTER(c_p), P_i64, P_i64, c_i, c_i, P_d, c_i, c_i, c_d, c_d,
+                                      c_u, c_p]),
+        "pe_sync_status": (c_i, [c_p]),
+        "pe_launch_count": (c_i64, []),
+        "pe_last_error": (ctypes.c_char_p, []),
+        "pe_release": (None, []),
+        "pe_debug_set": (c_i, [c_i, c_i64]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+def declared_symbols() -> List[str]:
+    """Entry points declared in include/polar_express.h."""
+    import re
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:int|int64_t|void|const char\*)\s+\**(pe_\w+)\s*\(", text, re.M)))
+
+
+def _check(code: int):
+    if code != PE_OK:
+        msg = lib().pe_last_error().decode(errors="replace")
+        raise PolarExpressError(code, msg)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ------------------------------------------------------------ offline stage
+
+def pe_coeffs(degree: int, l: float, T: int, safety: float = 1.01, cushion: Optional[float] = None,
+              skip_last: bool = False, return_info: bool = False):
+    """Coefficient table (T, 3) float64; with return_info also the bounds
+    (T+1, 2) and the Remez iteration count per step."""
+    coeffs = np.zeros((T, 3), dtype=np.float64)
+    bounds = np.zeros((T + 1, 2), dtype=np.float64)
+    iters = (ctypes.c_int * max(T, 1))()
+    flags = PE_SAFETY_SKIP_LAST if skip_last else 0
+    code = lib().pe_coeffs_ex(int(degree), float(l), int(T), float(safety),
+                              -1.0 if cushion is None else float(cushion), flags,
+                              _dptr(coeffs), _dptr(bounds), iters)
+    _check(code)
+    if return_info:
+        return coeffs, bounds, np.array(list(iters)[:T])
+    return coeffs
+
+
+# ------------------------------------------------------------- online stage
+
+def _table(table) -> np.ndarray:
+    t = np.ascontiguousarray(np.asarray(table, dtype=np.float64).reshape(-1, 3))
+    return t
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _io_of(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return PE_IO_FP32
+    if t.dtype == torch.bfloat16:
+        return PE_IO_BF16
+    raise PolarExpressError(PE_EINVAL, f"unsupported tensor dtype {t.dtype}")
+
+
+def _check_tensor(t):
+    if not t.is_cuda:
+        raise PolarExpressError(PE_EINVAL, "tensor must be on a CUDA device")
+    if t.dim() != 2:
+        raise PolarExpressError(PE_EINVAL, "tensor must be 2-D")
+    if t.stride(1) != 1:
+        raise PolarExpressError(PE_EINVAL, "tensor rows must be contiguous")
+
+
+def pe_polar(X, table, dtype: str = "bf16", stream=None, norm_scale: float = 1.01,
+             norm_eps: float = 1e-7):
+    """Overwrite the 2-D CUDA tensor X (float32 or bfloat16) with the Polar
+    Express approximation of polar(X). Asynchronous on ``stream``."""
+    _check_tensor(X)
+    tab = _table(table)
+    code = lib().pe_polar_ex(ctypes.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], X.stride(0), _io_of(X),
+                             _dptr(tab), tab.shape[0], DTYPES[dtype], float(norm_scale), float(norm_eps),
+                             ctypes.c_void_p(_stream_handle(stream)))
+    _check(code)
+    return X
+
+
+def pe_polar_batched(Xs: Sequence, table, dtype: str = "bf16", stream=None, flags: int = 0,
+                     norm_scale: float = 1.01, norm_eps: float = 1e-7):
+    """In place on a list of contiguous 2-D CUDA tensors of one dtype."""
+    if len(Xs) == 0:
+        return Xs
+    io = _io_of(Xs[0])
+    for t in Xs:
+        _check_tensor(t)
+        if not t.is_contiguous():
+            raise PolarExpressError(PE_EINVAL, "batched tensors must be contiguous")
+        if _io_of(t) != io:
+            raise PolarExpressError(PE_EINVAL, "batched tensors must share one dtype")
+    n = len(Xs)
+    ptrs = (ctypes.c_void_p * n)(*[t.data_ptr() for t in Xs])
+    ms = (ctypes.c_int64 * n)(*[t.shape[0] for t in Xs])
+    ns = (ctypes.c_int64 * n)(*[t.shape[1] for t in Xs])
+    tab = _table(table)
+    code = lib().pe_polar_batched_ex(ptrs, ms, ns, n, io, _dptr(tab), tab.shape[0], DTYPES[dtype],
+                                     float(norm_scale), float(norm_eps), int(flags),
+                                     ctypes.c_void_p(_stream_handle(stream)))
+    _check(code)
+    return Xs
+
+
+def pe_sync_status(stream=None) -> int:
+    """Synchronise the stream and return (and clear) the device status; raises
+    PolarExpressError for a non-OK status."""
+    code = lib().pe_sync_status(ctypes.c_void_p(_stream_handle(stream)))
+    _check(code)
+    return code
+
+
+def pe_launch_count() -> int:
+    return int(lib().pe_launch_count())
+
+
+def pe_release():
+    lib().pe_release()
+
+
+def pe_debug_set(key: int, value: int):
+    _check(lib().pe_debug_set(int(key), int(value)))
+
+
+def pe_version() -> int:
+    return int(lib().pe_version())

@@ -1,0 +1,503 @@
+// C ABI of the library: argument checks, workspace, cached plans (grouped
+// task lists, tensor maps, captured CUDA graphs) and the launch sequence of
+// the online stage (Alg. 1, online box):
+//   prepare (norm + scale + cast + transpose)  ->  T x [Gram -> A^2 -> update]
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <list>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pe_internal.h"
+#include "pe_umma.h"
+
+namespace pe {
+namespace {
+
+thread_local std::string g_err;
+std::mutex g_mu;
+std::atomic<int64_t> g_launches{0};
+int64_t g_dbg_withhold = -1;
+int64_t g_dbg_wait_ns = 0;
+bool g_dbg_fail_alloc = false;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return PE_ECUDA;
+}
+
+#define PE_CU(call)                                   \
+    do {                                              \
+        cudaError_t _e = (call);                      \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call); \
+    } while (0)
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+struct DeviceState {
+    bool init = false;
+    int sms = 0, major = 0, minor = 0;
+    int* status = nullptr;   // device status word (bit 0 timeout, bit 1 non-finite norm)
+    cudaStream_t cap = nullptr;  // private stream used to capture plans
+};
+std::vector<DeviceState> g_dev;
+
+int device_state(DeviceState** out) {
+    int dev = 0;
+    PE_CU(cudaGetDevice(&dev));
+    if ((int)g_dev.size() <= dev) g_dev.resize(dev + 1);
+    DeviceState& d = g_dev[dev];
+    if (!d.init) {
+        PE_CU(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+        PE_CU(cudaDeviceGetAttribute(&d.major, cudaDevAttrComputeCapabilityMajor, dev));
+        PE_CU(cudaDeviceGetAttribute(&d.minor, cudaDevAttrComputeCapabilityMinor, dev));
+        PE_CU(cudaMalloc(&d.status, 64));
+        PE_CU(cudaMemset(d.status, 0, 64));
+        PE_CU(cudaStreamCreateWithFlags(&d.cap, cudaStreamNonBlocking));
+        d.init = true;
+    }
+    *out = &d;
+    return PE_OK;
+}
+
+// ------------------------------------------------------------------ plans
+
+struct PlanKey {
+    int dev, dtype, T, io, count;
+    unsigned flags;
+    float scale, eps;
+    std::vector<uintptr_t> ptrs;
+    std::vector<int64_t> dims;   // m, n, ld per matrix
+    std::vector<float> coef;     // 3*T
+    bool operator==(const PlanKey& o) const {
+        return dev == o.dev && dtype == o.dtype && T == o.T && io == o.io && count == o.count &&
+               flags == o.flags && scale == o.scale && eps == o.eps && ptrs == o.ptrs &&
+               dims == o.dims && coef == o.coef;
+    }
+};
+
+struct Plan {
+    PlanKey key;
+    DeviceState* ds = nullptr;
+    std::vector<DevMat> mats;
+    char* ws = nullptr;           // one allocation: descriptors, task lists, buffers
+    size_t ws_bytes = 0;
+    DevMat* d_mats = nullptr;
+    NormTask* d_norm = nullptr;
+    int n_norm = 0;
+    double* d_partials = nullptr;
+    TileTask* d_prep = nullptr;
+    int n_prep = 0;
+    TileTask* d_tiles[3] = {nullptr, nullptr, nullptr};   // SIMT per-phase lists
+    int n_tiles[3] = {0, 0, 0};
+    int* d_counters = nullptr;
+    int n_counters = 0;
+    UmmaPlan umma;                // tcgen05 path (tensor maps, persistent schedule)
+    cudaGraphExec_t exec = nullptr;
+    int kernels_per_run = 0;
+    ~Plan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (ws) cudaFree(ws);
+    }
+};
+
+std::list<std::unique_ptr<Plan>> g_plans;   // most recently used first
+constexpr size_t kMaxPlans = 16;
+
+struct Carve {
+    size_t off = 0;
+    size_t take(size_t bytes, size_t align = 1024) {
+        off = round_up(off, align);
+        size_t o = off;
+        off += bytes;
+        return o;
+    }
+};
+
+int build_plan(const PlanKey& key, Plan** out) {
+    auto P = std::make_unique<Plan>();
+    P->key = key;
+    PE_CU(cudaGetDevice(&P->key.dev));
+    int st = device_state(&P->ds);
+    if (st != PE_OK) return st;
+    if (!(P->ds->major == 10 && P->ds->minor == 3))
+        return fail(PE_EUNSUPPORTED, "this library is built for sm_103 (GB300) only");
+
+    const int count = key.count;
+    const int dtype = key.dtype;
+    P->mats.resize(count);
+    Carve cv;
+    // layout of the single workspace allocation
+    const size_t o_mats = cv.take(sizeof(DevMat) * count, 64);
+    std::vector<NormTask> norm;
+    std::vector<TileTask> prep, tl[3];
+    struct Off { size_t xf, xf2, xh0, xh1, xl0, xl1, af, ah, al, bfp, bh, bl; };
+    std::vector<Off> offs(count);
+    int part = 0;
+    for (int i = 0; i < count; ++i) {
+        DevMat& M = P->mats[i];
+        memset(&M, 0, sizeof(M));
+        const int64_t m = key.dims[3 * i], n = key.dims[3 * i + 1], ld = key.dims[3 * i + 2];
+        M.user = reinterpret_cast<void*>(key.ptrs[i]);
+        M.ld = ld;
+        M.m = (int32_t)m;
+        M.n = (int32_t)n;
+        M.trans = m > n;
+        M.io = key.io;
+        M.s = (int32_t)std::min(m, n);
+        M.L = (int32_t)std::max(m, n);
+        M.sp = (int32_t)round_up(M.s, kPadS);
+        M.Lp = (int32_t)round_up(M.L, kPadL);
+        const int rows_per = (int)std::max<int64_t>(1, 32768 / n);
+        M.part0 = part;
+        for (int64_t r = 0; r < m; r += rows_per) {
+            norm.push_back(NormTask{i, (int32_t)r, (int32_t)std::min<int64_t>(m, r + rows_per), 0});
+            ++part;
+        }
+        M.npart = part - M.part0;
+        for (int a = 0; a < M.sp / 64; ++a)
+            for (int b = 0; b < M.Lp / 64; ++b) prep.push_back(TileTask{i, a, b, -1});
+        const size_t sL = (size_t)M.sp * M.Lp, ss = (size_t)M.sp * M.sp;
+        Off& o = offs[i];
+        memset(&o, 0, sizeof(o));
+        o.xf = cv.take(4 * sL);
+        if (dtype == PE_FP32) {
+            o.xf2 = cv.take(4 * sL);
+            o.af = cv.take(4 * ss);
+            o.bfp = cv.take(4 * ss);
+        } else {
+            o.xh0 = cv.take(2 * sL);
+            o.xh1 = cv.take(2 * sL);
+            o.af = cv.take(4 * ss);
+            o.ah = cv.take(2 * ss);
+            o.bh = cv.take(2 * ss);
+            if (dtype == PE_BF16X3) {
+                o.xl0 = cv.take(2 * sL);
+                o.xl1 = cv.take(2 * sL);
+                o.al = cv.take(2 * ss);
+                o.bl = cv.take(2 * ss);
+            }
+        }
+        if (dtype == PE_FP32) {
+            const int ts = M.sp / 128, tL = M.Lp / 128;
+            for (int a = 0; a < ts; ++a)
+                for (int b = a; b < ts; ++b) {
+                    tl[kGram].push_back(TileTask{i, a, b, kGram});
+                    tl[kSquare].push_back(TileTask{i, a, b, kSquare});
+                }
+            for (int a = 0; a < ts; ++a)
+                for (int b = 0; b < tL; ++b) tl[kApply].push_back(TileTask{i, a, b, kApply});
+        }
+    }
+    P->n_norm = (int)norm.size();
+    P->n_prep = (int)prep.size();
+    const size_t o_norm = cv.take(sizeof(NormTask) * norm.size(), 64);
+    const size_t o_part = cv.take(sizeof(double) * norm.size(), 64);
+    const size_t o_prep = cv.take(sizeof(TileTask) * prep.size(), 64);
+    size_t o_tl[3];
+    for (int k = 0; k < 3; ++k) {
+        P->n_tiles[k] = (int)tl[k].size();
+        o_tl[k] = cv.take(sizeof(TileTask) * std::max<size_t>(1, tl[k].size()), 64);
+    }
+    P->n_counters = 2 * count + 64;
+    const size_t o_cnt = cv.take(sizeof(int) * P->n_counters, 64);
+    size_t o_umma = 0, umma_bytes = 0;
+    if (dtype != PE_FP32) {
+        umma_bytes = umma_workspace_bytes(P->mats.data(), count);
+        o_umma = cv.take(umma_bytes, 1024);
+    }
+    P->ws_bytes = cv.off;
+    if (g_dbg_fail_alloc) {
+        g_dbg_fail_alloc = false;
+        return fail(PE_ENOMEM, "workspace allocation failed (injected)");
+    }
+    cudaError_t e = cudaMalloc(&P->ws, P->ws_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        P->ws = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? PE_ENOMEM : PE_ECUDA,
+                    std::string("workspace allocation of ") + std::to_string(P->ws_bytes) +
+                        " bytes failed: " + cudaGetErrorString(e));
+    }
+    char* base = P->ws;
+    for (int i = 0; i < count; ++i) {
+        DevMat& M = P->mats[i];
+        const Off& o = offs[i];
+        M.xf = reinterpret_cast<float*>(base + o.xf);
+        if (dtype == PE_FP32) {
+            M.xf2 = reinterpret_cast<float*>(base + o.xf2);
+            M.af = reinterpret_cast<float*>(base + o.af);
+            M.bfp = reinterpret_cast<float*>(base + o.bfp);
+        } else {
+            M.xh[0] = reinterpret_cast<bf16*>(base + o.xh0);
+            M.xh[1] = reinterpret_cast<bf16*>(base + o.xh1);
+            M.af = reinterpret_cast<float*>(base + o.af);
+            M.ah = reinterpret_cast<bf16*>(base + o.ah);
+            M.bh = reinterpret_cast<bf16*>(base + o.bh);
+            if (dtype == PE_BF16X3) {
+                M.xl[0] = reinterpret_cast<bf16*>(base + o.xl0);
+                M.xl[1] = reinterpret_cast<bf16*>(base + o.xl1);
+                M.al = reinterpret_cast<bf16*>(base + o.al);
+                M.bl = reinterpret_cast<bf16*>(base + o.bl);
+            }
+        }
+    }
+    P->d_mats = reinterpret_cast<DevMat*>(base + o_mats);
+    P->d_norm = reinterpret_cast<NormTask*>(base + o_norm);
+    P->d_partials = reinterpret_cast<double*>(base + o_part);
+    P->d_prep = reinterpret_cast<TileTask*>(base + o_prep);
+    for (int k = 0; k < 3; ++k) P->d_tiles[k] = reinterpret_cast<TileTask*>(base + o_tl[k]);
+    P->d_counters = reinterpret_cast<int*>(base + o_cnt);
+    PE_CU(cudaMemcpy(P->d_mats, P->mats.data(), sizeof(DevMat) * count, cudaMemcpyHostToDevice));
+    PE_CU(cudaMemcpy(P->d_norm, norm.data(), sizeof(NormTask) * norm.size(), cudaMemcpyHostToDevice));
+    PE_CU(cudaMemcpy(P->d_prep, prep.data(), sizeof(TileTask) * prep.size(), cudaMemcpyHostToDevice));
+    for (int k = 0; k < 3; ++k)
+        if (!tl[k].empty())
+            PE_CU(cudaMemcpy(P->d_tiles[k], tl[k].data(), sizeof(TileTask) * tl[k].size(),
+                             cudaMemcpyHostToDevice));
+    PE_CU(cudaMemset(P->d_counters, 0, sizeof(int) * P->n_counters));
+    if (dtype != PE_FP32) {
+        const bool tune = !(key.flags & PE_BATCH_NO_TUNE);
+        int ust = umma_build(&P->umma, P->mats.data(), P->d_mats, count, dtype, P->ds->sms,
+                             base + o_umma, umma_bytes, P->d_counters, tune, &g_err);
+        if (ust != PE_OK) return ust;
+    }
+    *out = P.release();
+    return PE_OK;
+}
+
+// Enqueue the whole online stage of a plan on `st`.
+int enqueue(Plan* P, cudaStream_t st) {
+    const PlanKey& k = P->key;
+    int nk = 0;
+    int outputs = kPrepF32;
+    if (k.dtype != PE_FP32) outputs |= kPrepBF16;
+    if (k.dtype == PE_BF16X3) outputs |= kPrepBF16Lo;
+    PE_CU(launch_norm_partials(P->d_mats, P->d_norm, P->n_norm, P->d_partials, st));
+    ++nk;
+    PE_CU(launch_prepare(P->d_mats, P->d_prep, P->n_prep, P->d_partials, k.scale, k.eps, outputs,
+                         P->ds->status, P->d_counters, P->n_counters, st));
+    ++nk;
+    for (int t = 0; t < k.T; ++t) {
+        const float a = k.coef[3 * t], b = k.coef[3 * t + 1], c = k.coef[3 * t + 2];
+        const int last = (t == k.T - 1);
+        if (k.dtype == PE_FP32) {
+            for (int ph = 0; ph < 3; ++ph) {
+                PE_CU(launch_simt_phase(P->d_mats, P->d_tiles[ph], P->n_tiles[ph], ph, a, b, c, t & 1,
+                                        last, st));
+                ++nk;
+            }
+        } else {
+            const bool phased = (k.flags & PE_BATCH_PHASED) != 0;
+            int withhold = (int)g_dbg_withhold;
+            int n_launched = 0;
+            cudaError_t e = umma_step(&P->umma, t, a, b, c, last, phased, withhold,
+                                      (uint64_t)g_dbg_wait_ns, P->ds->status, st, &n_launched);
+            if (e != cudaSuccess) return cuda_fail(e, "umma_step");
+            nk += n_launched;
+        }
+    }
+    g_dbg_withhold = -1;
+    P->kernels_per_run = nk;
+    return PE_OK;
+}
+
+int get_plan(const PlanKey& key, cudaStream_t st, Plan** out, bool* fresh) {
+    for (auto it = g_plans.begin(); it != g_plans.end(); ++it) {
+        if ((*it)->key == key) {
+            g_plans.splice(g_plans.begin(), g_plans, it);
+            *out = g_plans.front().get();
+            *fresh = false;
+            return PE_OK;
+        }
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    PE_CU(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(PE_EINVAL, "no cached plan for this call while the stream is capturing; "
+                               "run the call once before capturing it");
+    Plan* p = nullptr;
+    int r = build_plan(key, &p);
+    if (r != PE_OK) return r;
+    g_plans.emplace_front(p);
+    while (g_plans.size() > kMaxPlans) {
+        cudaDeviceSynchronize();
+        g_plans.pop_back();
+    }
+    *out = p;
+    *fresh = true;
+    return PE_OK;
+}
+
+int run(void* const* X, const int64_t* m, const int64_t* n, const int64_t* ld, int count, int io,
+        const double* table, int T, int dtype, double scale, double eps, unsigned flags, void* stream) {
+    if (!X || !m || !n) return fail(PE_EINVAL, "NULL argument");
+    if (count < 1 || count > kMaxMatrices) return fail(PE_EINVAL, "count must be in 1..4096");
+    if (!table) return fail(PE_EINVAL, "table is NULL");
+    if (T < 1 || T > kMaxSteps) return fail(PE_EINVAL, "T must be in 1..64");
+    if (dtype != PE_FP32 && dtype != PE_BF16 && dtype != PE_BF16X3) return fail(PE_EINVAL, "bad dtype");
+    if (io != PE_IO_FP32 && io != PE_IO_BF16) return fail(PE_EINVAL, "bad io_type");
+    if (!(std::isfinite(scale) && scale > 0) || !(std::isfinite(eps) && eps >= 0))
+        return fail(PE_EINVAL, "norm_scale must be > 0 and norm_eps >= 0");
+    PlanKey key;
+    key.dtype = dtype;
+    key.T = T;
+    key.io = io;
+    key.count = count;
+    key.flags = flags;
+    key.scale = (float)scale;
+    key.eps = (float)eps;
+    key.ptrs.resize(count);
+    key.dims.resize(3 * count);
+    for (int i = 0; i < count; ++i) {
+        if (!X[i]) return fail(PE_EINVAL, "matrix pointer " + std::to_string(i) + " is NULL");
+        const int64_t ldi = ld ? ld[i] : n[i];
+        if (m[i] < 1 || n[i] < 1) return fail(PE_EINVAL, "sizes must be >= 1");
+        if (m[i] > (1 << 20) || n[i] > (1 << 20) || m[i] * n[i] > (int64_t)1 << 31)
+            return fail(PE_EINVAL, "matrix too large (m, n <= 2^20, m*n <= 2^31)");
+        if (ldi < n[i]) return fail(PE_EINVAL, "ld must be >= n");
+        const size_t esz = io == PE_IO_BF16 ? 2 : 4;
+        if (reinterpret_cast<uintptr_t>(X[i]) % esz) return fail(PE_EINVAL, "misaligned matrix pointer");
+        key.ptrs[i] = reinterpret_cast<uintptr_t>(X[i]);
+        key.dims[3 * i] = m[i];
+        key.dims[3 * i + 1] = n[i];
+        key.dims[3 * i + 2] = ldi;
+    }
+    key.coef.resize(3 * T);
+    for (int i = 0; i < 3 * T; ++i) {
+        if (!std::isfinite(table[i])) return fail(PE_EINVAL, "non-finite coefficient in table");
+        key.coef[i] = (float)table[i];
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    PE_CU(cudaGetDevice(&key.dev));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Plan* P = nullptr;
+    bool fresh = false;
+    int r = get_plan(key, st, &P, &fresh);
+    if (r != PE_OK) return r;
+    const bool use_graph = !(flags & PE_BATCH_NO_GRAPH) && count > 1;
+    if (!use_graph || g_dbg_withhold >= 0) {
+        r = enqueue(P, st);
+        if (r != PE_OK) return r;
+        g_launches += P->kernels_per_run;
+        return PE_OK;
+    }
+    if (!P->exec) {
+        cudaGraph_t g = nullptr;
+        cudaStream_t cap = P->ds->cap;
+        PE_CU(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        r = enqueue(P, cap);
+        cudaError_t ee = cudaStreamEndCapture(cap, &g);
+        if (r != PE_OK) {
+            if (g) cudaGraphDestroy(g);
+            return r;
+        }
+        if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
+        ee = cudaGraphInstantiate(&P->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ee != cudaSuccess) {
+            P->exec = nullptr;
+            return cuda_fail(ee, "cudaGraphInstantiate");
+        }
+    }
+    PE_CU(cudaGraphLaunch(P->exec, st));
+    g_launches += P->kernels_per_run;
+    return PE_OK;
+}
+
+}  // namespace
+}  // namespace pe
+
+extern "C" {
+
+int pe_version(void) { return 10000; }
+
+int pe_coeffs(int degree, double l, int T, double safety, double* coeffs, double* bounds) {
+    return pe_coeffs_ex(degree, l, T, safety, -1.0, 0u, coeffs, bounds, nullptr);
+}
+
+int pe_coeffs_ex(int degree, double l, int T, double safety, double cushion, unsigned flags,
+                 double* coeffs, double* bounds, int* remez_iters) {
+    const char* why = "";
+    int r = pe::coeffs_table(degree, l, T, safety, cushion, flags, coeffs, bounds, remez_iters, &why);
+    if (r != PE_OK) pe::g_err = why;
+    return r;
+}
+
+int pe_polar(void* X, int64_t m, int64_t n, const double* table, int T, int dtype, void* stream) {
+    return pe_polar_ex(X, m, n, n, PE_IO_FP32, table, T, dtype, 1.01, 1e-7, stream);
+}
+
+int pe_polar_ex(void* X, int64_t m, int64_t n, int64_t ld, int io_type, const double* table, int T,
+                int dtype, double norm_scale, double norm_eps, void* stream) {
+    void* xs[1] = {X};
+    int64_t ms[1] = {m}, ns[1] = {n}, lds[1] = {ld};
+    return pe::run(xs, ms, ns, lds, 1, io_type, table, T, dtype, norm_scale, norm_eps,
+                   PE_BATCH_NO_GRAPH, stream);
+}
+
+int pe_polar_batched(void* const* X, const int64_t* m, const int64_t* n, int count,
+                     const double* table, int T, int dtype, void* stream) {
+    return pe::run(X, m, n, nullptr, count, PE_IO_FP32, table, T, dtype, 1.01, 1e-7, 0u, stream);
+}
+
+int pe_polar_batched_ex(void* const* X, const int64_t* m, const int64_t* n, int count, int io_type,
+                        const double* table, int T, int dtype, double norm_scale, double norm_eps,
+                        unsigned flags, void* stream) {
+    return pe::run(X, m, n, nullptr, count, io_type, table, T, dtype, norm_scale, norm_eps, flags,
+                   stream);
+}
+
+int pe_sync_status(void* stream) {
+    std::lock_guard<std::mutex> lk(pe::g_mu);
+    pe::DeviceState* d = nullptr;
+    int r = pe::device_state(&d);
+    if (r != PE_OK) return r;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return pe::cuda_fail(e, "cudaStreamSynchronize");
+    int h = 0;
+    e = cudaMemcpy(&h, d->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return pe::cuda_fail(e, "reading the status word");
+    e = cudaMemset(d->status, 0, sizeof(int));
+    if (e != cudaSuccess) return pe::cuda_fail(e, "clearing the status word");
+    if (h & 1) return pe::fail(PE_ETIMEOUT, "a bounded device wait expired; results are invalid");
+    if (h & 2) return pe::fail(PE_ECUDA, "non-finite Frobenius norm in the input");
+    return PE_OK;
+}
+
+int64_t pe_launch_count(void) { return pe::g_launches.load(); }
+
+const char* pe_last_error(void) { return pe::g_err.c_str(); }
+
+void pe_release(void) {
+    std::lock_guard<std::mutex> lk(pe::g_mu);
+    if (!pe::g_plans.empty()) cudaDeviceSynchronize();
+    pe::g_plans.clear();
+}
+
+int pe_debug_set(int key, int64_t value) {
+    std::lock_guard<std::mutex> lk(pe::g_mu);
+    switch (key) {
+        case 1: pe::g_dbg_withhold = value; return PE_OK;
+        case 2: pe::g_dbg_wait_ns = value < 0 ? 0 : value; return PE_OK;
+        case 3: pe::g_dbg_fail_alloc = value != 0; return PE_OK;
+        default: return pe::fail(PE_EINVAL, "unknown debug key");
+    }
+}
+
+}  // extern "C"

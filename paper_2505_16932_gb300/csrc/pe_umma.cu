@@ -1,0 +1,808 @@
+// BF16 / split-BF16 tensor-core path of one polynomial step (Sec. 3.5 Horner
+// form; App. A online code):
+//   Gram    A  = X X^T          tiles (i <= j) of 128 x 128, mirrored store
+//   square  B  = b A + c A A    tiles (i <= j) of 128 x 128, mirrored store
+//   update  X' = a X + B X      tiles of 128 x 256
+// on sm_103a tcgen05 tensor cores: operands staged in shared memory by TMA
+// (128-byte swizzle, 4-stage mbarrier ring), accumulators in TMEM (two
+// 256-column buffers), warp-specialised roles:
+//   warp 0     TMA producer (one lane)
+//   warp 1     TMEM allocator + MMA issuer (one lane)
+//   warps 2-5  epilogue: tcgen05.ld -> FP32 epilogue arithmetic -> global
+// The kernel is persistent and grouped: each CTA walks its own list of tiles
+// (all matrices of the call, phase-ordered Gram -> square -> update). In the
+// fused mode one launch runs the whole step, and a square/update tile waits
+// (bounded, on a per-matrix counter) until every Gram/square tile of its
+// matrix has been stored.
+//
+// Split BF16 (BF16x3): every operand is x = hi + lo with hi = bf16(x),
+// lo = bf16(x - hi); each k-step issues hi*hi + hi*lo + lo*hi into the same
+// FP32 TMEM accumulator.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <queue>
+#include <string>
+#include <vector>
+
+#include "pe_internal.h"
+#include "pe_umma.h"
+
+namespace pe {
+namespace {
+
+constexpr int kThreads = 192;
+constexpr int kBM = 128;        // UMMA M
+constexpr int kBK = 64;         // k-block: one 128-byte swizzle row of BF16
+constexpr int kSymBN = 128;     // Gram / square tile width
+constexpr int kApplyBN = 256;   // update tile width
+constexpr int kTmemCols = 512;  // two 256-column accumulators
+constexpr int kMapsPerMat = 12;
+constexpr int kABytes = kBM * kBK * 2;        // 16 KB
+constexpr int kBBytes = kApplyBN * kBK * 2;   // 32 KB (max)
+constexpr uint64_t kDefaultWaitNs = 1000000000ull;  // 1 s
+
+enum MapIdx {
+    kMapXK0 = 0, kMapXK1 = 1, kMapXM0 = 2, kMapXM1 = 3, kMapA = 4, kMapB = 5,
+    kLo = 6   // lo maps follow at +6
+};
+
+struct StepArgs {
+    const DevMat* mats;
+    const CUtensorMap* maps;
+    const int* off;
+    const TileTask* tiles;
+    const int* need;
+    int* counters;
+    int* status;
+    float a, b, c;
+    int step, cur, last, dependent, withhold;
+    uint64_t wait_ns;
+};
+
+// ------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase. Returns false when the wait limit
+// passes or another role of the CTA has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit,
+                                          volatile int* abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (abort_flag && *abort_flag) return false;
+        if (globaltimer() - t0 > limit) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13,
+// leading-dimension byte offset >> 4 in 16-29, stride-dimension byte offset
+// >> 4 in 32-45, descriptor version 1 in bits 46-47, swizzle mode in 61-63
+// (2 = 128-byte swizzle).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// Instruction descriptor, kind::f16: D format F32 (bits 4-5 = 1), A and B
+// BF16 (bits 7-9 = 1, 10-12 = 1), A K-major (bit 15 = 0), B major in bit 16,
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N, bool b_mn_major) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((b_mn_major ? 1u : 0u) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Bounded wait for a readiness counter (fused mode). On expiry the status
+// word records a timeout and the caller proceeds: the launch always ends,
+// with invalid results that pe_sync_status reports.
+__device__ void wait_counter(const int* cnt, int target, uint64_t limit, int* status) {
+    if (ld_acquire(cnt) >= target) return;
+    const uint64_t t0 = globaltimer();
+    unsigned ns = 32;
+    while (ld_acquire(cnt) < target) {
+        if (*reinterpret_cast<volatile int*>(status) & 1) return;
+        if (globaltimer() - t0 > limit) {
+            atomicOr(status, 1);
+            return;
+        }
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;
+    }
+}
+
+struct Geo {
+    int kind, mat, tm, tn, bn, nkb;
+    int mapA, mapB;      // hi maps
+    int ya;              // A-operand row coordinate
+    int b0;              // B-operand row (K-major) or column (MN-major) origin
+};
+
+__device__ __forceinline__ Geo tile_geo(const TileTask& tk, const DevMat& M, int cur) {
+    Geo g;
+    g.kind = tk.kind;
+    g.mat = tk.mat;
+    g.tm = tk.tm;
+    g.tn = tk.tn;
+    g.ya = tk.tm * kBM;
+    if (tk.kind == kGram) {
+        g.bn = kSymBN;
+        g.nkb = M.Lp / kBK;
+        g.mapA = g.mapB = cur ? kMapXK1 : kMapXK0;
+        g.b0 = tk.tn * kSymBN;
+    } else if (tk.kind == kSquare) {
+        g.bn = kSymBN;
+        g.nkb = M.sp / kBK;
+        g.mapA = g.mapB = kMapA;
+        g.b0 = tk.tn * kSymBN;
+    } else {
+        g.b0 = tk.tn * kApplyBN;
+        g.bn = min(kApplyBN, M.Lp - g.b0);
+        g.nkb = M.sp / kBK;
+        g.mapA = kMapB;
+        g.mapB = cur ? kMapXM1 : kMapXM0;
+    }
+    return g;
+}
+
+__device__ __forceinline__ void put_bf16(bf16* hi, bf16* lo, int64_t idx, float v) {
+    const bf16 h = __float2bfloat16_rn(v);
+    hi[idx] = h;
+    if (lo) lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+__device__ __forceinline__ void store_user(const DevMat& M, int i, int l, float v) {
+    if (i >= M.s || l >= M.L) return;
+    const int64_t idx = M.trans ? (int64_t)l * M.ld + i : (int64_t)i * M.ld + l;
+    if (M.io == PE_IO_BF16) reinterpret_cast<bf16*>(M.user)[idx] = __float2bfloat16_rn(v);
+    else reinterpret_cast<float*>(M.user)[idx] = v;
+}
+
+// Epilogue of one 32-column chunk for TMEM lane (= tile row) r.
+template <int NS>
+__device__ __forceinline__ void epilogue_chunk(const Geo& g, const DevMat& M, const StepArgs& A, int r,
+                                               int col0, float (&v)[32]) {
+    const int gi = g.tm * kBM + r;
+    if (g.kind == kApply) {
+        const int nxt = A.cur ^ 1;
+        float* xrow = M.xf + (int64_t)gi * M.Lp + col0;
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+            const float4 x4 = *reinterpret_cast<const float4*>(xrow + j);
+            v[j + 0] = fmaf(A.a, x4.x, v[j + 0]);
+            v[j + 1] = fmaf(A.a, x4.y, v[j + 1]);
+            v[j + 2] = fmaf(A.a, x4.z, v[j + 2]);
+            v[j + 3] = fmaf(A.a, x4.w, v[j + 3]);
+        }
+        if (A.last) {
+#pragma unroll 4
+            for (int j = 0; j < 32; ++j) store_user(M, gi, col0 + j, v[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+                *reinterpret_cast<float4*>(xrow + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            bf16* hrow = M.xh[nxt] + (int64_t)gi * M.Lp + col0;
+            bf16* lrow = (NS == 3) ? M.xl[nxt] + (int64_t)gi * M.Lp + col0 : nullptr;
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+                __align__(16) bf16 h[8];
+                __align__(16) bf16 lo[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    h[q] = __float2bfloat16_rn(v[j + q]);
+                    if (NS == 3) lo[q] = __float2bfloat16_rn(v[j + q] - __bfloat162float(h[q]));
+                }
+                *reinterpret_cast<uint4*>(hrow + j) = *reinterpret_cast<const uint4*>(h);
+                if (NS == 3) *reinterpret_cast<uint4*>(lrow + j) = *reinterpret_cast<const uint4*>(lo);
+            }
+        }
+        return;
+    }
+    // symmetric kinds: Gram writes A (FP32 + BF16 [+ lo]); square writes B
+    if (g.kind == kSquare) {
+        const float* arow = M.af + (int64_t)gi * M.sp + col0;
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+            const float4 a4 = *reinterpret_cast<const float4*>(arow + j);
+            v[j + 0] = fmaf(A.b, a4.x, A.c * v[j + 0]);
+            v[j + 1] = fmaf(A.b, a4.y, A.c * v[j + 1]);
+            v[j + 2] = fmaf(A.b, a4.z, A.c * v[j + 2]);
+            v[j + 3] = fmaf(A.b, a4.w, A.c * v[j + 3]);
+        }
+    }
+    float* f32 = (g.kind == kGram) ? M.af : nullptr;
+    bf16* hi = (g.kind == kGram) ? M.ah : M.bh;
+    bf16* lo = (NS == 3) ? ((g.kind == kGram) ? M.al : M.bl) : nullptr;
+    const bool diag = (g.tm == g.tn);
+    if (!diag) {
+        if (f32) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+                *reinterpret_cast<float4*>(f32 + (int64_t)gi * M.sp + col0 + j) =
+                    make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; j += 8) {
+            __align__(16) bf16 h[8];
+            __align__(16) bf16 l8[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                h[q] = __float2bfloat16_rn(v[j + q]);
+                if (NS == 3) l8[q] = __float2bfloat16_rn(v[j + q] - __bfloat162float(h[q]));
+            }
+            *reinterpret_cast<uint4*>(hi + (int64_t)gi * M.sp + col0 + j) = *reinterpret_cast<const uint4*>(h);
+            if (NS == 3)
+                *reinterpret_cast<uint4*>(lo + (int64_t)gi * M.sp + col0 + j) = *reinterpret_cast<const uint4*>(l8);
+        }
+        // mirror: lanes hold consecutive rows, so each store is coalesced
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+            const int64_t mi = (int64_t)(col0 + j) * M.sp + gi;
+            if (f32) f32[mi] = v[j];
+            put_bf16(hi, lo, mi, v[j]);
+        }
+    } else {
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+            const int gj = col0 + j;
+            if (gj >= gi) {
+                const int64_t di = (int64_t)gi * M.sp + gj;
+                if (f32) f32[di] = v[j];
+                put_bf16(hi, lo, di, v[j]);
+            }
+            if (gj > gi) {
+                const int64_t mi = (int64_t)gj * M.sp + gi;
+                if (f32) f32[mi] = v[j];
+                put_bf16(hi, lo, mi, v[j]);
+            }
+        }
+    }
+}
+
+template <int NS>
+struct Cfg {
+    static constexpr int kStages = (NS == 1) ? 4 : 2;
+    // stage layout: A hi | [A lo] | B hi | [B lo]
+    static constexpr int kAOps = (NS == 1) ? 1 : 2;
+    static constexpr int kStage = kAOps * (kABytes + kBBytes);
+    static constexpr int kBarOff = kStages * kStage;
+    static constexpr size_t kSmem = 1024 + kBarOff + 256;
+};
+
+template <int NS>
+__global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_constant__ StepArgs A) {
+    using C = Cfg<NS>;
+    constexpr int NST = C::kStages;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kBarOff);
+    uint64_t* empty = full + NST;
+    uint64_t* tfull = empty + NST;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t limit = A.wait_ns ? A.wait_ns : kDefaultWaitNs;
+    const int t_begin = A.off[blockIdx.x], t_end = A.off[blockIdx.x + 1];
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&tfull[s], 1);
+            mbar_init(&tempty[s], 128);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------------ producer
+        int stage = 0;
+        uint32_t phase = 0;
+        uint32_t issued = 0;   // bit s: stage s has been issued at least once
+        uint32_t last_par = 0; // bit s: parity of the last issue of stage s
+        bool ok = true;
+        for (int it = t_begin; it < t_end && ok; ++it) {
+            const TileTask tk = A.tiles[it];
+            const DevMat& M = A.mats[tk.mat];
+            const Geo g = tile_geo(tk, M, A.cur);
+            const CUtensorMap* mp = A.maps + (size_t)tk.mat * kMapsPerMat;
+            if (A.dependent && g.kind != kGram) {
+                const int which = (g.kind == kSquare) ? 0 : 1;
+                wait_counter(A.counters + 2 * g.mat + which, (A.step + 1) * A.need[2 * g.mat + which], limit,
+                             A.status);
+                fence_proxy_async_global();
+            }
+            const uint32_t bbytes = (uint32_t)g.bn * kBK * 2;
+            const uint32_t tx = (uint32_t)C::kAOps * (kABytes + bbytes);
+            for (int kb = 0; kb < g.nkb; ++kb) {
+                if (!mbar_wait(&empty[stage], phase ^ 1, limit, abort_flag)) { ok = false; break; }
+                mbar_expect_tx(&full[stage], tx);
+                const uint32_t sbase = smem_u32(smem + stage * C::kStage);
+                const int kx = kb * kBK;
+#pragma unroll
+                for (int o = 0; o < C::kAOps; ++o) {
+                    const int lo_off = o ? kLo : 0;
+                    const uint32_t a_dst = sbase + o * kABytes;
+                    const uint32_t b_dst = sbase + C::kAOps * kABytes + o * kBBytes;
+                    tma_load_2d(a_dst, mp + g.mapA + lo_off, &full[stage], kx, g.ya);
+                    if (g.kind == kApply) {
+                        for (int j = 0; j < g.bn / 64; ++j)
+                            tma_load_2d(b_dst + j * (64 * kBK * 2), mp + g.mapB + lo_off, &full[stage],
+                                        g.b0 + j * 64, kx);
+                    } else {
+                        tma_load_2d(b_dst, mp + g.mapB + lo_off, &full[stage], kx, g.b0);
+                    }
+                }
+                issued |= 1u << stage;
+                last_par = (last_par & ~(1u << stage)) | (phase << stage);
+                if (++stage == NST) { stage = 0; phase ^= 1; }
+            }
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicOr(A.status, 4);
+            // let every issued copy land before the CTA can exit
+            for (int s = 0; s < NST; ++s)
+                if (issued & (1u << s)) mbar_wait(&full[s], (last_par >> s) & 1u, limit, nullptr);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------------ MMA issuer
+        int stage = 0;
+        uint32_t phase = 0;
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        bool ok = true;
+        for (int it = t_begin; it < t_end && ok; ++it) {
+            const TileTask tk = A.tiles[it];
+            const DevMat& M = A.mats[tk.mat];
+            const Geo g = tile_geo(tk, M, A.cur);
+            if (!mbar_wait(&tempty[acc], acc_phase ^ 1, limit, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t d_tmem = tmem_base + acc * 256;
+            const bool mn = (g.kind == kApply);
+            const uint32_t idesc = idesc_bf16(kBM, g.bn, mn);
+            for (int kb = 0; kb < g.nkb; ++kb) {
+                if (!mbar_wait(&full[stage], phase, limit, abort_flag)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t sbase = smem_u32(smem + stage * C::kStage);
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk) {
+#pragma unroll
+                    for (int p = 0; p < (NS == 1 ? 1 : 3); ++p) {
+                        // products: hi*hi, hi*lo, lo*hi
+                        const int ao = (p == 2) ? 1 : 0;
+                        const int bo = (p == 1) ? 1 : 0;
+                        const uint32_t a_addr = sbase + ao * kABytes + kk * 32;
+                        const uint64_t adesc = sdesc(a_addr, 16, 1024);
+                        const uint32_t b_base = sbase + C::kAOps * kABytes + bo * kBBytes;
+                        uint64_t bdesc;
+                        if (mn) bdesc = sdesc(b_base + kk * 16 * 128, 64 * kBK * 2, 1024);
+                        else bdesc = sdesc(b_base + kk * 32, 16, 1024);
+                        umma_bf16(d_tmem, adesc, bdesc, idesc, (kb | kk | p) != 0);
+                    }
+                }
+                umma_commit(&empty[stage]);
+                if (++stage == NST) { stage = 0; phase ^= 1; }
+            }
+            if (!ok) break;
+            umma_commit(&tfull[acc]);
+            acc ^= 1;
+            if (acc == 0) acc_phase ^= 1;
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicOr(A.status, 4);
+            umma_commit(drain);
+            mbar_wait(drain, 0, limit, nullptr);
+        }
+    } else if (warp >= 2) {
+        // ------------------------------------------------------ epilogue
+        const int q = warp & 3;            // TMEM lane quarter this warp may access
+        const int r = q * 32 + lane;       // tile row
+        const int etid = threadIdx.x - 64; // 0..127
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (int it = t_begin; it < t_end; ++it) {
+            const TileTask tk = A.tiles[it];
+            const DevMat& M = A.mats[tk.mat];
+            const Geo g = tile_geo(tk, M, A.cur);
+            if (!mbar_wait(&tfull[acc], acc_phase, limit, abort_flag)) {
+                *abort_flag = 1;
+                atomicOr(A.status, 4);
+                break;
+            }
+            tc_fence_after();
+            if (A.dependent && g.kind == kSquare)   // A (FP32) comes from other CTAs
+                wait_counter(A.counters + 2 * g.mat, (A.step + 1) * A.need[2 * g.mat], limit, A.status);
+            const int nch = g.bn / 32;
+            const int colbase = (g.kind == kApply) ? g.tn * kApplyBN : g.tn * kSymBN;
+            for (int ch = 0; ch < nch; ++ch) {
+                float v[32];
+                tmem_ld32(tmem_base + acc * 256 + ((uint32_t)(q * 32) << 16) + ch * 32, v);
+                if (ch == nch - 1) {
+                    tc_fence_before();
+                    mbar_arrive(&tempty[acc]);
+                }
+                epilogue_chunk<NS>(g, M, A, r, colbase + ch * 32, v);
+            }
+            if (A.dependent && g.kind != kApply) {
+                __threadfence();
+                epi_bar();
+                if (etid == 0 && !(g.kind == kGram && g.mat == A.withhold))
+                    red_release_add(A.counters + 2 * g.mat + (g.kind == kSquare ? 1 : 0), 1);
+            }
+            acc ^= 1;
+            if (acc == 0) acc_phase ^= 1;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols));
+    }
+}
+
+// ----------------------------------------------------------------- host
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn(std::string* err) {
+    static EncodeTiledFn fn = nullptr;
+    if (fn) return fn;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) {
+        *err = "cuTensorMapEncodeTiled is not available from the driver";
+        return nullptr;
+    }
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+    return fn;
+}
+
+// BF16 row-major rows x cols (cols contiguous), box = box_cols x box_rows.
+bool make_map(EncodeTiledFn enc, CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows,
+              int box_cols) {
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+struct HostTile {
+    TileTask t;
+    double cost;
+};
+
+void tiles_of(const DevMat& M, int i, std::vector<HostTile>* ph) {
+    const int ts = M.sp / kBM;
+    for (int a = 0; a < ts; ++a)
+        for (int b = a; b < ts; ++b) {
+            ph[kGram].push_back(HostTile{TileTask{i, a, b, kGram}, (double)kBM * kSymBN * M.Lp});
+            ph[kSquare].push_back(HostTile{TileTask{i, a, b, kSquare}, (double)kBM * kSymBN * M.sp});
+        }
+    const int tn = (M.Lp + kApplyBN - 1) / kApplyBN;
+    for (int a = 0; a < ts; ++a)
+        for (int b = 0; b < tn; ++b) {
+            const int bn = std::min(kApplyBN, M.Lp - b * kApplyBN);
+            ph[kApply].push_back(HostTile{TileTask{i, a, b, kApply}, (double)kBM * bn * M.sp});
+        }
+}
+
+// Longest-processing-time assignment of an ordered tile list to `grid` CTAs;
+// each CTA keeps the list order (phase order), which the readiness waits
+// rely on for progress.
+void lpt_assign(const std::vector<HostTile>& order, int grid, std::vector<int>* off, std::vector<TileTask>* out) {
+    std::vector<std::vector<TileTask>> per(grid);
+    typedef std::pair<double, int> Load;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
+    for (int c = 0; c < grid; ++c) pq.push(Load(0.0, c));
+    for (const HostTile& h : order) {
+        Load l = pq.top();
+        pq.pop();
+        per[l.second].push_back(h.t);
+        l.first += h.cost + 2.0e5;   // + per-tile fixed overhead
+        pq.push(l);
+    }
+    off->assign(grid + 1, 0);
+    out->clear();
+    for (int c = 0; c < grid; ++c) {
+        (*off)[c] = (int)out->size();
+        out->insert(out->end(), per[c].begin(), per[c].end());
+    }
+    (*off)[grid] = (int)out->size();
+}
+
+void sort_phase(std::vector<HostTile>& v) {
+    std::stable_sort(v.begin(), v.end(), [](const HostTile& x, const HostTile& y) { return x.cost > y.cost; });
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+size_t umma_workspace_bytes(const DevMat* mats, int count) {
+    size_t tiles = 0;
+    for (int i = 0; i < count; ++i) {
+        const int ts = mats[i].sp / kBM;
+        const int tn = (mats[i].Lp + kApplyBN - 1) / kApplyBN;
+        tiles += (size_t)ts * (ts + 1) + (size_t)ts * tn;
+    }
+    size_t b = 0;
+    b += align_up(sizeof(CUtensorMap) * kMapsPerMat * count, 1024);
+    b += 2 * align_up(sizeof(TileTask) * (tiles + 1), 256);   // fused + phased lists
+    b += 4 * align_up(sizeof(int) * (1024 + 1), 256);         // CSR offsets
+    b += align_up(sizeof(int) * 2 * count, 256);
+    return b + 4096;
+}
+
+int umma_build(UmmaPlan* P, const DevMat* mats, const DevMat* d_mats, int count, int dtype, int sms, char* ws,
+               size_t ws_bytes, int* counters, bool tune, std::string* err) {
+    (void)tune;
+    EncodeTiledFn enc = encode_fn(err);
+    if (!enc) return PE_EUNSUPPORTED;
+    P->count = count;
+    P->dtype = dtype;
+    P->nsplit = (dtype == PE_BF16X3) ? 3 : 1;
+    P->d_mats = d_mats;
+    P->counters = counters;
+    std::vector<CUtensorMap> maps(kMapsPerMat * count);
+    memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
+    std::vector<HostTile> ph[3];
+    std::vector<int> need(2 * count);
+    for (int i = 0; i < count; ++i) {
+        const DevMat& M = mats[i];
+        CUtensorMap* mp = maps.data() + (size_t)i * kMapsPerMat;
+        bool ok = true;
+        for (int lo = 0; lo < (P->nsplit == 3 ? 2 : 1); ++lo) {
+            bf16* const* x = lo ? M.xl : M.xh;
+            const int o = lo ? kLo : 0;
+            ok &= make_map(enc, mp + o + kMapXK0, x[0], M.sp, M.Lp, kBM, kBK);
+            ok &= make_map(enc, mp + o + kMapXK1, x[1], M.sp, M.Lp, kBM, kBK);
+            ok &= make_map(enc, mp + o + kMapXM0, x[0], M.sp, M.Lp, kBK, 64);
+            ok &= make_map(enc, mp + o + kMapXM1, x[1], M.sp, M.Lp, kBK, 64);
+            ok &= make_map(enc, mp + o + kMapA, lo ? M.al : M.ah, M.sp, M.sp, kBM, kBK);
+            ok &= make_map(enc, mp + o + kMapB, lo ? M.bl : M.bh, M.sp, M.sp, kBM, kBK);
+        }
+        if (!ok) {
+            *err = "cuTensorMapEncodeTiled failed for matrix " + std::to_string(i);
+            return PE_ECUDA;
+        }
+        const size_t g0 = ph[kGram].size(), s0 = ph[kSquare].size();
+        tiles_of(M, i, ph);
+        need[2 * i] = (int)(ph[kGram].size() - g0);
+        need[2 * i + 1] = (int)(ph[kSquare].size() - s0);
+    }
+    for (int k = 0; k < 3; ++k) sort_phase(ph[k]);
+    std::vector<HostTile> fused;
+    for (int k = 0; k < 3; ++k) fused.insert(fused.end(), ph[k].begin(), ph[k].end());
+    P->ntiles = (int)fused.size();
+    P->grid = std::max(1, std::min(sms, P->ntiles));
+    std::vector<int> off;
+    std::vector<TileTask> list;
+    lpt_assign(fused, P->grid, &off, &list);
+
+    size_t o = 0;
+    char* base = ws;
+    auto take = [&](size_t bytes, size_t al) { o = align_up(o, al); char* p = base + o; o += bytes; return p; };
+    P->maps = take(sizeof(CUtensorMap) * maps.size(), 1024);
+    P->tiles = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (list.size() + 1), 256));
+    P->tile_off = reinterpret_cast<int*>(take(sizeof(int) * (off.size()), 256));
+    P->need = reinterpret_cast<int*>(take(sizeof(int) * 2 * count, 256));
+    cudaError_t e = cudaMemcpy(P->maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->tiles, list.data(), sizeof(TileTask) * list.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->tile_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->need, need.data(), sizeof(int) * need.size(), cudaMemcpyHostToDevice);
+    // phased schedules: one list per phase, concatenated after the fused one
+    TileTask* ph_base = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (list.size() + 1), 256));
+    size_t ph_pos = 0;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        std::vector<int> poff;
+        std::vector<TileTask> plist;
+        const int g = std::max(1, std::min(sms, (int)ph[k].size()));
+        lpt_assign(ph[k], g, &poff, &plist);
+        P->grid_phase[k] = ph[k].empty() ? 0 : g;
+        P->ph_tiles[k] = ph_base + ph_pos;
+        P->ph_off[k] = reinterpret_cast<int*>(take(sizeof(int) * poff.size(), 256));
+        if (!plist.empty())
+            e = cudaMemcpy(P->ph_tiles[k], plist.data(), sizeof(TileTask) * plist.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(P->ph_off[k], poff.data(), sizeof(int) * poff.size(), cudaMemcpyHostToDevice);
+        ph_pos += plist.size();
+    }
+    if (e != cudaSuccess) {
+        *err = std::string("uploading the tile schedule: ") + cudaGetErrorString(e);
+        return PE_ECUDA;
+    }
+    if (o > ws_bytes) {
+        *err = "internal: tcgen05 workspace too small";
+        return PE_ECUDA;
+    }
+    P->smem_bytes = (P->nsplit == 3) ? Cfg<3>::kSmem : Cfg<1>::kSmem;
+    e = cudaFuncSetAttribute(umma_step_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<1>::kSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(umma_step_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<3>::kSmem);
+    if (e != cudaSuccess) {
+        *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+        return PE_ECUDA;
+    }
+    return PE_OK;
+}
+
+cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, bool phased, int withhold,
+                      uint64_t wait_ns, int* status, cudaStream_t st, int* launched) {
+    StepArgs A;
+    A.mats = P->d_mats;
+    A.maps = reinterpret_cast<const CUtensorMap*>(P->maps);
+    A.need = P->need;
+    A.counters = P->counters;
+    A.status = status;
+    A.a = a;
+    A.b = b;
+    A.c = c;
+    A.step = t;
+    A.cur = t & 1;
+    A.last = last;
+    A.withhold = withhold;
+    A.wait_ns = wait_ns;
+    *launched = 0;
+    auto go = [&](int grid, bool coop) -> cudaError_t {
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = P->smem_bytes;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = coop ? 1 : 0;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        ++*launched;
+        if (P->nsplit == 3) return cudaLaunchKernelEx(&cfg, umma_step_kernel<3>, A);
+        return cudaLaunchKernelEx(&cfg, umma_step_kernel<1>, A);
+    };
+    if (!phased) {
+        A.off = P->tile_off;
+        A.tiles = P->tiles;
+        A.dependent = 1;
+        return go(P->grid, true);
+    }
+    A.dependent = 0;
+    for (int k = 0; k < 3; ++k) {
+        if (!P->grid_phase[k]) continue;
+        A.off = P->ph_off[k];
+        A.tiles = P->ph_tiles[k];
+        cudaError_t e = go(P->grid_phase[k], false);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace pe

@@ -1,0 +1,46 @@
+// tcgen05 (UMMA) path of the online stage: BF16 and split-BF16 (BF16x3).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "pe_internal.h"
+
+namespace pe {
+
+// Host-side plan of the persistent grouped step kernel.
+struct UmmaPlan {
+    int count = 0;
+    int dtype = 0;
+    int nsplit = 1;          // 1 (BF16) or 3 (BF16x3)
+    int grid = 0;            // persistent CTAs (<= SMs)
+    int grid_phase[3] = {0, 0, 0};
+    void* maps = nullptr;    // device array of CUtensorMap, kMapsPerMat per matrix
+    int* tile_off = nullptr; // device CSR offsets per CTA (grid + 1), fused schedule
+    TileTask* tiles = nullptr;
+    int ntiles = 0;
+    int* ph_off[3] = {nullptr, nullptr, nullptr};  // per-phase schedules (phased mode)
+    TileTask* ph_tiles[3] = {nullptr, nullptr, nullptr};
+    int* need = nullptr;     // device: per matrix [n_gram, n_square]
+    int* counters = nullptr; // device: per matrix [gram_done, square_done]
+    const DevMat* d_mats = nullptr;
+    size_t smem_bytes = 0;
+    int apply_bn = 256;
+};
+
+size_t umma_workspace_bytes(const DevMat* mats, int count);
+
+// Builds tensor maps and schedules inside `ws` (device memory of
+// umma_workspace_bytes()); d_mats already holds the descriptors.
+int umma_build(UmmaPlan* P, const DevMat* mats, const DevMat* d_mats, int count, int dtype, int sms,
+               char* ws, size_t ws_bytes, int* counters, bool tune, std::string* err);
+
+// Enqueue polynomial step t (0-based). Phased mode runs three grouped
+// launches; otherwise one persistent launch with per-matrix readiness waits.
+cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, bool phased,
+                      int withhold, uint64_t wait_ns, int* status, cudaStream_t st, int* launched);
+
+}  // namespace pe

@@ -1,0 +1,100 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+* the library builds, loads without a GPU driver, and exports every entry
+  point that include/polar_express.h declares;
+* pe_coeffs (C++ FP64 solver) reproduces the oracle's table bit for bit over
+  a grid of degrees, lower bounds, step counts and safety settings;
+* argument errors are reported synchronously with a message.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2505_16932_gb300 as pe
+from paper_2505_16932_gb300 import build as B
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return pe.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    declared = pe.declared_symbols()
+    assert "pe_coeffs" in declared and "pe_polar" in declared and "pe_polar_batched" in declared
+    for name in declared:
+        assert hasattr(L, name), name
+    assert pe.pe_version() >= 10000
+
+
+GRID = [(d, l, T, s) for d in (3, 5)
+        for l in (1e-7, 1e-5, 1e-4, 1e-3, 0.02407327424182761, 0.03, 0.1, 0.5, 1.0)
+        for T in (1, 2, 5, 8, 12, 16)
+        for s in (1.0, 1.01)]
+
+
+@pytest.mark.parametrize("degree,l,T,safety", GRID)
+def test_coeffs_bit_exact_vs_oracle(L, degree, l, T, safety):
+    tab, bounds, iters = pe.pe_coeffs(degree, l, T, safety, return_info=True)
+    rows, ob, info = O.optimal_composition(l, T, degree=degree, safety=safety, return_info=True)
+    assert tab.tolist() == [list(r) for r in rows]
+    assert bounds.tolist() == [list(b) for b in ob]
+
+
+@pytest.mark.parametrize("cushion", [0.0, 0.1, 0.05])
+def test_coeffs_cushion_and_skip_last(L, cushion):
+    tab = pe.pe_coeffs(5, 1e-3, 6, 1.01, cushion=cushion, skip_last=True)
+    rows, _ = O.optimal_composition(1e-3, 6, cushion=cushion, safety=1.01, safety_skip_last=True)
+    assert tab.tolist() == [list(r) for r in rows]
+
+
+def test_coeffs_remez_iterations(L):
+    _, _, iters = pe.pe_coeffs(5, 1e-3, 10, 1.01, return_info=True)
+    for t, it in enumerate(iters):
+        assert 0 <= it <= 5
+    assert iters[-1] == 0          # converged rows take the NS shortcut
+
+
+@pytest.mark.parametrize("args", [(4, 1e-3, 5, 1.01), (5, 0.0, 5, 1.01), (5, 1.5, 5, 1.01),
+                                  (5, 1e-3, 0, 1.01), (5, 1e-3, 65, 1.01), (5, 1e-3, 5, 0.9),
+                                  (5, float("nan"), 5, 1.01)])
+def test_coeffs_argument_errors(L, args):
+    with pytest.raises(pe.PolarExpressError) as ei:
+        pe.pe_coeffs(*args)
+    assert ei.value.code == pe.PE_EINVAL
+    assert L.pe_last_error().decode()
+
+
+def test_coeffs_null_output(L):
+    assert L.pe_coeffs(5, 1e-3, 5, 1.01, None, None) == pe.PE_EINVAL
+
+
+def test_debug_key_errors(L):
+    assert L.pe_debug_set(99, 0) == pe.PE_EINVAL
+
+
+def test_polar_argument_errors_without_gpu(L):
+    """Argument validation happens before any CUDA call, so it works here."""
+    tab = np.ones((5, 3))
+    P = ctypes.POINTER(ctypes.c_double)
+    tp = tab.ctypes.data_as(P)
+    # NULL matrix
+    assert L.pe_polar(None, 4, 4, tp, 5, pe.PE_BF16, None) == pe.PE_EINVAL
+    # bad sizes / T / dtype
+    fake = ctypes.c_void_p(0x10000)
+    assert L.pe_polar(fake, 0, 4, tp, 5, pe.PE_BF16, None) == pe.PE_EINVAL
+    assert L.pe_polar(fake, 4, 4, tp, 0, pe.PE_BF16, None) == pe.PE_EINVAL
+    assert L.pe_polar(fake, 4, 4, tp, 5, 7, None) == pe.PE_EINVAL
+    assert L.pe_polar(fake, 4, 4, None, 5, pe.PE_BF16, None) == pe.PE_EINVAL
+    bad = np.array([[1.0, float("inf"), 0.0]])
+    assert L.pe_polar(fake, 4, 4, bad.ctypes.data_as(P), 1, pe.PE_BF16, None) == pe.PE_EINVAL
+    assert L.pe_polar_ex(fake, 4, 4, 3, 0, tp, 5, 0, 1.01, 1e-7, None) == pe.PE_EINVAL   # ld < n
+    assert L.pe_polar_ex(fake, 4, 4, 4, 0, tp, 5, 0, -1.0, 1e-7, None) == pe.PE_EINVAL  # scale
+    ptrs = (ctypes.c_void_p * 1)(None)
+    ms = (ctypes.c_int64 * 1)(4)
+    assert L.pe_polar_batched(ptrs, ms, ms, 1, tp, 5, pe.PE_BF16, None) == pe.PE_EINVAL
+    assert L.pe_polar_batched(ptrs, ms, ms, 0, tp, 5, pe.PE_BF16, None) == pe.PE_EINVAL

@@ -1,0 +1,256 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances (relative Frobenius distance to the FP64 iteration on the same
+input): FP32 path 1e-5, BF16 path 2e-2 (the method's stated parity bars).
+Single-product checks isolate each kernel with one-row tables:
+(1,0,0) -> X_0, (0,1,0) -> A X_0, (0,0,1) -> A^2 X_0, compared with FP64
+products of the same rounded operands.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+torch = pytest.importorskip("torch")
+import paper_2505_16932_gb300 as pe  # noqa: E402
+from paper_2505_16932_gb300 import build as B  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+BF16_TOL = 2e-2
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    pe.lib()
+    yield
+    torch.cuda.synchronize()
+
+
+def to_dev(G, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(G, dtype=np.float32)).to("cuda").to(dtype)
+
+
+def run_single(G, table, dtype, io=torch.float32):
+    X = to_dev(G, io)
+    pe.pe_polar(X, table, dtype)
+    pe.pe_sync_status()
+    return X.float().cpu().numpy().astype(np.float64)
+
+
+def bf16r(x):
+    """Round to bfloat16 (nearest even) through torch, as FP64."""
+    return torch.from_numpy(np.asarray(x, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def table(l, T, safety=1.01):
+    return pe.pe_coeffs(5, l, T, safety)
+
+
+# ----------------------------------------------------------- plain method
+
+def test_fp32_plain_small_matches_oracle():
+    wl = synth.plain_small()
+    G = wl.matrices[0]
+    tab = table(wl.l, wl.T)
+    got = run_single(G, tab, "fp32")
+    ref = O.polar_express(G.astype(np.float32).astype(np.float64), tab)
+    assert O.rel_fro(got, ref) <= FP32_TOL
+    # the error metrics of the output against polar(G) are those of the FP64 iteration
+    P = O.polar_svd(G)
+    assert abs(O.err_polar_fro(got, P) - O.err_polar_fro(ref, P)) <= 1e-5
+
+
+SHAPES = [(1, 1), (1, 5), (5, 1), (37, 100), (100, 37), (129, 300), (300, 129), (256, 256), (257, 513),
+          (640, 130)]
+
+
+@pytest.mark.parametrize("m,n", SHAPES)
+def test_fp32_shapes(m, n):
+    case = synth.random_svd_case(seed=m * 1000 + n, m=m, n=n, lo=1e-2)
+    tab = table(1e-3, 6)
+    got = run_single(case.G, tab, "fp32")
+    ref = O.polar_express_spectral(case.U, case.s, case.V, tab)
+    assert got.shape == (m, n)
+    assert O.rel_fro(got, ref) <= FP32_TOL
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "bf16", "bf16x3"])
+@pytest.mark.parametrize("m,n", [(200, 333), (333, 200), (128, 256)])
+def test_identity_step(dtype, m, n):
+    """Table (1, 0, 0): the output is the normalised input (prepare + store)."""
+    rng = np.random.default_rng(m + n)
+    G = rng.standard_normal((m, n))
+    got = run_single(G, [(1.0, 0.0, 0.0)], dtype)
+    ref = G.astype(np.float32) / (1.01 * np.linalg.norm(G.astype(np.float32)) + 1e-7)
+    assert np.max(np.abs(got - ref)) <= 1e-6 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "bf16", "bf16x3"])
+@pytest.mark.parametrize("m,n", [(256, 640), (640, 256), (384, 384), (130, 700)])
+@pytest.mark.parametrize("row", [(0.0, 1.0, 0.0), (0.0, 0.0, 1.0), (0.5, -1.0, 0.7)])
+def test_single_products(dtype, m, n, row):
+    rng = np.random.default_rng(7 * m + n)
+    G = rng.standard_normal((m, n))
+    got = run_single(G, [row], dtype)
+    X0 = G.astype(np.float32).astype(np.float64)
+    X0 = X0 / (1.01 * np.linalg.norm(X0) + 1e-7)
+    if m > n:
+        X0 = X0.T
+    a, b, c = row
+    if dtype == "bf16":
+        Xh = bf16r(X0)
+        A = Xh @ Xh.T
+        Ah = bf16r(A)
+        Bm = bf16r(b * A + c * (Ah @ Ah))
+        ref = a * X0 + Bm @ Xh
+        tol = 1e-2
+    else:
+        A = X0 @ X0.T
+        ref = a * X0 + (b * A + c * (A @ A)) @ X0
+        tol = 1e-5 if dtype == "fp32" else 1e-4
+    if m > n:
+        ref = ref.T
+    assert O.rel_fro(got, ref) <= tol
+
+
+# ------------------------------------------------------------ BF16 paths
+
+def test_bf16_gpt2_layer_batched_vs_oracle():
+    """One GPT-2-small layer (768x2304, 768x768, 768x3072, 3072x768), T = 5,
+    grouped launch, against the FP64 iteration (spectral form)."""
+    wl = synth.gpt2_small(layers=1)
+    tab = table(wl.l, wl.T)
+    Xs = [to_dev(G) for G in wl.matrices]
+    pe.pe_polar_batched(Xs, tab, "bf16")
+    pe.pe_sync_status()
+    for X, sv in zip(Xs, wl.svd):
+        got = X.cpu().numpy().astype(np.float64)
+        ref = O.polar_express_spectral(sv.U, sv.s, sv.V, tab)
+        assert O.rel_fro(got, ref) <= BF16_TOL
+
+
+def test_bf16x3_closer_than_bf16():
+    case = synth.random_svd_case(seed=11, m=384, n=640, lo=1e-3)
+    tab = table(1e-3, 6)
+    ref = O.polar_express_spectral(case.U, case.s, case.V, tab)
+    e16 = O.rel_fro(run_single(case.G, tab, "bf16"), ref)
+    e3 = O.rel_fro(run_single(case.G, tab, "bf16x3"), ref)
+    assert e16 <= BF16_TOL
+    assert e3 <= 1e-3 and e3 < e16 / 4
+
+
+def test_bf16_io_bf16():
+    case = synth.random_svd_case(seed=12, m=300, n=500, lo=1e-2)
+    tab = table(1e-3, 5)
+    G16 = bf16r(case.G)
+    got = run_single(G16, tab, "bf16", io=torch.bfloat16)
+    ref = O.polar_express(G16, tab)
+    assert O.rel_fro(got, ref) <= BF16_TOL
+
+
+# ------------------------------------------- grouped, graph, determinism
+
+def _uneven(seed=3, k=7):
+    rng = np.random.default_rng(seed)
+    shapes = [(int(rng.integers(1, 700)), int(rng.integers(1, 700))) for _ in range(k)] + [(128, 1024), (1024, 128)]
+    return [rng.standard_normal(s) for s in shapes]
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "bf16", "bf16x3"])
+def test_grouped_equals_single_bitwise(dtype):
+    mats = _uneven()
+    tab = table(1e-3, 5)
+    singles = [run_single(G, tab, dtype) for G in mats]
+    for flags in (0, pe.PE_BATCH_PHASED, pe.PE_BATCH_NO_GRAPH):
+        Xs = [to_dev(G) for G in mats]
+        pe.pe_polar_batched(Xs, tab, dtype, flags=flags)
+        pe.pe_sync_status()
+        for X, ref in zip(Xs, singles):
+            assert np.array_equal(X.cpu().numpy().astype(np.float64), ref)
+
+
+def test_graph_replay_repeats():
+    mats = _uneven(seed=5)
+    tab = table(1e-3, 5)
+    Xs = [to_dev(G) for G in mats]
+    pe.pe_polar_batched(Xs, tab, "bf16")
+    first = [X.clone() for X in Xs]
+    n0 = pe.pe_launch_count()
+    for _ in range(3):
+        for X, G in zip(Xs, mats):
+            X.copy_(to_dev(G))
+        pe.pe_polar_batched(Xs, tab, "bf16")
+    pe.pe_sync_status()
+    assert pe.pe_launch_count() > n0
+    for X, F in zip(Xs, first):
+        assert torch.equal(X, F)
+
+
+def test_batched_vs_oracle_uneven():
+    mats = _uneven(seed=9)
+    tab = table(1e-3, 6)
+    for dtype, tol in (("fp32", FP32_TOL), ("bf16", BF16_TOL)):
+        Xs = [to_dev(G) for G in mats]
+        pe.pe_polar_batched(Xs, tab, dtype)
+        pe.pe_sync_status()
+        for X, G in zip(Xs, mats):
+            ref = O.polar_express(G.astype(np.float32).astype(np.float64), tab)
+            assert O.rel_fro(X.cpu().numpy().astype(np.float64), ref) <= (tol if dtype == "fp32" else 3e-2)
+
+
+# ---------------------------------------------------- status / failures
+
+def test_nonfinite_input_reports_status():
+    G = np.ones((64, 64))
+    G[3, 5] = np.inf
+    X = to_dev(G)
+    pe.pe_polar(X, table(1e-3, 2), "bf16")
+    with pytest.raises(pe.PolarExpressError) as ei:
+        pe.pe_sync_status()
+    assert ei.value.code == pe.PE_ECUDA
+    # the status was cleared; the next call works
+    run_single(np.eye(64), table(1e-3, 2), "bf16")
+
+
+def test_readiness_wait_timeout_reports_status():
+    """Withhold matrix 0's Gram readiness in one fused launch: its waiters'
+    bounded waits expire, the launch completes, PE_ETIMEOUT is reported, and
+    the library keeps working afterwards."""
+    mats = _uneven(seed=13)
+    tab = table(1e-3, 3)
+    Xs = [to_dev(G) for G in mats]
+    pe.pe_debug_set(2, 20_000_000)       # 20 ms wait limit
+    pe.pe_debug_set(1, 0)                # withhold matrix 0
+    pe.pe_polar_batched(Xs, tab, "bf16")
+    with pytest.raises(pe.PolarExpressError) as ei:
+        pe.pe_sync_status()
+    assert ei.value.code == pe.PE_ETIMEOUT
+    pe.pe_debug_set(2, 0)
+    Xs = [to_dev(G) for G in mats]
+    pe.pe_polar_batched(Xs, tab, "bf16")
+    pe.pe_sync_status()
+    ref = O.polar_express(mats[1].astype(np.float32).astype(np.float64), tab)
+    assert O.rel_fro(Xs[1].cpu().numpy().astype(np.float64), ref) <= 3e-2
+
+
+def test_injected_alloc_failure():
+    pe.pe_debug_set(3, 1)
+    X = to_dev(np.random.default_rng(0).standard_normal((77, 55)))
+    with pytest.raises(pe.PolarExpressError) as ei:
+        pe.pe_polar(X, table(1e-3, 2), "bf16")
+    assert ei.value.code == pe.PE_ENOMEM
+
+
+def test_empty_and_bad_shapes_rejected():
+    X = torch.zeros((0, 5), device="cuda")
+    with pytest.raises(pe.PolarExpressError):
+        pe.pe_polar(X, table(1e-3, 2), "bf16")
+    assert pe.pe_polar_batched([], table(1e-3, 2), "bf16") == []
