@@ -18,8 +18,8 @@
  *    enqueue work on `stream` (a cudaStream_t passed as void*; NULL is the
  *    legacy default stream) and return. Failures that only the device can
  *    see (a bounded wait that expired, a non-finite norm) are latched in a
- *    per-device status word and reported by pe_sync_status() and by the next
- *    device call, as PE_ETIMEOUT or PE_ECUDA.
+ *    per-device status word and reported (then cleared) by pe_sync_status(),
+ *    as PE_ETIMEOUT or PE_ECUDA.
  *  - Matrices are dense row-major: element (i, j) of an m x n matrix with
  *    leading dimension ld lives at base[i * ld + j].
  *  - Workspace is owned by the library: a per-device pool that grows on
@@ -197,6 +197,22 @@ int pe_sync_status(void* stream);
  * graphs) on the calling process since load; for launch accounting. */
 int64_t pe_launch_count(void);
 
+/*
+ * Tracing: per-kernel device time. While tracing is on, device calls enqueue
+ * their kernels directly (no graph) and bracket every launch with a pair of
+ * CUDA events recorded on the call's stream.
+ *   pe_trace_enable(1) clears the record and starts tracing; (0) stops it.
+ *   pe_trace_read synchronises the recorded events and writes, for kernel
+ *   kind k < nkinds, launches[k] and ms[k] (total device milliseconds):
+ *     0 norm partials, 1 prepare, 2 FP32 Gram, 3 FP32 square, 4 FP32 update,
+ *     5 tcgen05 fused step, 6 tcgen05 Gram phase, 7 tcgen05 square phase,
+ *     8 tcgen05 update phase.
+ *   Returns PE_EINVAL for NULL outputs or nkinds < 1.
+ */
+#define PE_TRACE_KINDS 9
+int pe_trace_enable(int on);
+int pe_trace_read(int64_t* launches, double* ms, int nkinds);
+
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char* pe_last_error(void);
 
@@ -212,6 +228,9 @@ void pe_release(void);
  *          invalid results and PE_ETIMEOUT is latched.
  *   key 2: wait limit of the persistent kernel in nanoseconds (0 = default).
  *   key 3: make the next workspace allocation fail (value != 0).
+ *   key 4: device address of a buffer of 16 int64 per persistent CTA that
+ *          tcgen05 launches fill with per-role cycle counters (0 disables;
+ *          while set, calls enqueue directly, without a graph).
  * Returns PE_EINVAL for an unknown key.
  */
 int pe_debug_set(int key, int64_t value);

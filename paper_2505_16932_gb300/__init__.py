@@ -78,6 +78,8 @@ def lib() -> ctypes.CDLL:
         "pe_last_error": (ctypes.c_char_p, []),
         "pe_release": (None, []),
         "pe_debug_set": (c_i, [c_i, c_i64]),
+        "pe_trace_enable": (c_i, [c_i]),
+        "pe_trace_read": (c_i, [P_i64, P_d, c_i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -203,6 +205,23 @@ def pe_sync_status(stream=None) -> int:
 
 def pe_launch_count() -> int:
     return int(lib().pe_launch_count())
+
+
+TRACE_KINDS = ["norm_partials", "prepare", "simt_gram", "simt_square", "simt_update", "umma_step",
+               "umma_gram", "umma_square", "umma_update"]
+
+
+def pe_trace_enable(on: bool = True):
+    _check(lib().pe_trace_enable(1 if on else 0))
+
+
+def pe_trace_read() -> dict:
+    """{kernel kind: (launches, total ms)} for the traced launches."""
+    n = len(TRACE_KINDS)
+    cnt = (ctypes.c_int64 * n)()
+    ms = (ctypes.c_double * n)()
+    _check(lib().pe_trace_read(cnt, ms, n))
+    return {k: (int(cnt[i]), float(ms[i])) for i, k in enumerate(TRACE_KINDS) if cnt[i]}
 
 
 def pe_release():

@@ -29,6 +29,43 @@ std::atomic<int64_t> g_launches{0};
 int64_t g_dbg_withhold = -1;
 int64_t g_dbg_wait_ns = 0;
 bool g_dbg_fail_alloc = false;
+void* g_dbg_prof = nullptr;
+
+// tracing: (kind, start, stop) event triples recorded on the call's stream
+struct TraceRec { int kind; cudaEvent_t a, b; };
+bool g_trace = false;
+std::vector<TraceRec> g_trace_recs;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t trace_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct TraceScope {
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    TraceScope(int k, cudaStream_t s) : kind(k), st(s) {
+        if (g_trace) {
+            a = trace_event();
+            cudaEventRecord(a, st);
+        }
+    }
+    ~TraceScope() {
+        if (a) {
+            cudaEvent_t b = trace_event();
+            cudaEventRecord(b, st);
+            g_trace_recs.push_back(TraceRec{kind, a, b});
+        }
+    }
+};
 
 int fail(int code, const std::string& msg) {
     g_err = msg;
@@ -287,16 +324,23 @@ int enqueue(Plan* P, cudaStream_t st) {
     int outputs = kPrepF32;
     if (k.dtype != PE_FP32) outputs |= kPrepBF16;
     if (k.dtype == PE_BF16X3) outputs |= kPrepBF16Lo;
-    PE_CU(launch_norm_partials(P->d_mats, P->d_norm, P->n_norm, P->d_partials, st));
+    {
+        TraceScope ts(0, st);
+        PE_CU(launch_norm_partials(P->d_mats, P->d_norm, P->n_norm, P->d_partials, st));
+    }
     ++nk;
-    PE_CU(launch_prepare(P->d_mats, P->d_prep, P->n_prep, P->d_partials, k.scale, k.eps, outputs,
-                         P->ds->status, P->d_counters, P->n_counters, st));
+    {
+        TraceScope ts(1, st);
+        PE_CU(launch_prepare(P->d_mats, P->d_prep, P->n_prep, P->d_partials, k.scale, k.eps, outputs,
+                             P->ds->status, P->d_counters, P->n_counters, st));
+    }
     ++nk;
     for (int t = 0; t < k.T; ++t) {
         const float a = k.coef[3 * t], b = k.coef[3 * t + 1], c = k.coef[3 * t + 2];
         const int last = (t == k.T - 1);
         if (k.dtype == PE_FP32) {
             for (int ph = 0; ph < 3; ++ph) {
+                TraceScope ts(2 + ph, st);
                 PE_CU(launch_simt_phase(P->d_mats, P->d_tiles[ph], P->n_tiles[ph], ph, a, b, c, t & 1,
                                         last, st));
                 ++nk;
@@ -305,8 +349,21 @@ int enqueue(Plan* P, cudaStream_t st) {
             const bool phased = (k.flags & PE_BATCH_PHASED) != 0;
             int withhold = (int)g_dbg_withhold;
             int n_launched = 0;
-            cudaError_t e = umma_step(&P->umma, t, a, b, c, last, phased, withhold,
-                                      (uint64_t)g_dbg_wait_ns, P->ds->status, st, &n_launched);
+            cudaError_t e = cudaSuccess;
+            P->umma.prof = g_dbg_prof;
+            if (!phased) {
+                TraceScope ts(5, st);
+                e = umma_step(&P->umma, t, a, b, c, last, -1, withhold, (uint64_t)g_dbg_wait_ns,
+                              P->ds->status, st, &n_launched);
+            } else {
+                for (int ph = 0; ph < 3 && e == cudaSuccess; ++ph) {
+                    TraceScope ts(6 + ph, st);
+                    int nl = 0;
+                    e = umma_step(&P->umma, t, a, b, c, last, ph, withhold, (uint64_t)g_dbg_wait_ns,
+                                  P->ds->status, st, &nl);
+                    n_launched += nl;
+                }
+            }
             if (e != cudaSuccess) return cuda_fail(e, "umma_step");
             nk += n_launched;
         }
@@ -390,7 +447,7 @@ int run(void* const* X, const int64_t* m, const int64_t* n, const int64_t* ld, i
     int r = get_plan(key, st, &P, &fresh);
     if (r != PE_OK) return r;
     const bool use_graph = !(flags & PE_BATCH_NO_GRAPH) && count > 1;
-    if (!use_graph || g_dbg_withhold >= 0) {
+    if (!use_graph || g_dbg_withhold >= 0 || g_trace || g_dbg_prof) {
         r = enqueue(P, st);
         if (r != PE_OK) return r;
         g_launches += P->kernels_per_run;
@@ -482,6 +539,36 @@ int pe_sync_status(void* stream) {
 
 int64_t pe_launch_count(void) { return pe::g_launches.load(); }
 
+int pe_trace_enable(int on) {
+    std::lock_guard<std::mutex> lk(pe::g_mu);
+    for (auto& r : pe::g_trace_recs) {
+        cudaEventSynchronize(r.b);
+        pe::g_event_pool.push_back(r.a);
+        pe::g_event_pool.push_back(r.b);
+    }
+    pe::g_trace_recs.clear();
+    pe::g_trace = on != 0;
+    return PE_OK;
+}
+
+int pe_trace_read(int64_t* launches, double* ms, int nkinds) {
+    if (!launches || !ms || nkinds < 1) return pe::fail(PE_EINVAL, "bad trace_read arguments");
+    std::lock_guard<std::mutex> lk(pe::g_mu);
+    for (int k = 0; k < nkinds; ++k) { launches[k] = 0; ms[k] = 0.0; }
+    for (auto& r : pe::g_trace_recs) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) return pe::cuda_fail(e, "cudaEventSynchronize");
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess) return pe::cuda_fail(e, "cudaEventElapsedTime");
+        if (r.kind < nkinds) {
+            launches[r.kind] += 1;
+            ms[r.kind] += t;
+        }
+    }
+    return PE_OK;
+}
+
 const char* pe_last_error(void) { return pe::g_err.c_str(); }
 
 void pe_release(void) {
@@ -496,6 +583,7 @@ int pe_debug_set(int key, int64_t value) {
         case 1: pe::g_dbg_withhold = value; return PE_OK;
         case 2: pe::g_dbg_wait_ns = value < 0 ? 0 : value; return PE_OK;
         case 3: pe::g_dbg_fail_alloc = value != 0; return PE_OK;
+        case 4: pe::g_dbg_prof = reinterpret_cast<void*>(value); return PE_OK;
         default: return pe::fail(PE_EINVAL, "unknown debug key");
     }
 }

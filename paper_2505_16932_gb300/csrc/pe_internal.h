@@ -39,6 +39,7 @@ struct DevMat {
     int32_t s, L;        // logical short / long side
     int32_t sp, Lp;      // padded sizes (multiples of kPadS / kPadL)
     int32_t part0, npart;  // range of this matrix's norm partials
+    int32_t out_tma;       // 1 when the caller's buffer admits TMA stores
     float* xf;           // FP32 X (master; updated in place on BF16 paths)
     float* xf2;          // FP32 ping-pong partner (FP32 path)
     bf16* xh[2];         // BF16 X (hi part), ping-pong

@@ -1,19 +1,32 @@
 // BF16 / split-BF16 tensor-core path of one polynomial step (Sec. 3.5 Horner
-// form; App. A online code):
-//   Gram    A  = X X^T          tiles (i <= j) of 128 x 128, mirrored store
-//   square  B  = b A + c A A    tiles (i <= j) of 128 x 128, mirrored store
-//   update  X' = a X + B X      tiles of 128 x 256
+// form; App. A online code), all on 128 x 256 output tiles:
+//   Gram    A  = X X^T          tiles touching the upper triangle, mirrored
+//   square  B  = b A + c A A    tiles touching the upper triangle, mirrored
+//   update  X' = a X + B X
 // on sm_103a tcgen05 tensor cores: operands staged in shared memory by TMA
-// (128-byte swizzle, 4-stage mbarrier ring), accumulators in TMEM (two
-// 256-column buffers), warp-specialised roles:
+// (128-byte swizzle, mbarrier ring), accumulators in TMEM (two 256-column
+// buffers), warp-specialised roles:
 //   warp 0     TMA producer (one lane)
 //   warp 1     TMEM allocator + MMA issuer (one lane)
-//   warps 2-5  epilogue: tcgen05.ld -> FP32 epilogue arithmetic -> global
+//   warps 2-9  epilogue, two warpgroups (one per half of the tile's
+//              columns); each warp owns 32 tile rows (its TMEM lane quarter)
+//              and works in 32 x 32 chunks.
+// BF16 epilogue: every chunk goes TMEM -> registers -> FP32 arithmetic ->
+// swizzled shared-memory staging -> TMA bulk tensor stores; the FP32 operand
+// of the epilogue (X for the update, A for the square) is fetched ahead by
+// TMA into the warp's staging buffer. Split-BF16 epilogue: the same
+// arithmetic with direct global stores.
+//
 // The kernel is persistent and grouped: each CTA walks its own list of tiles
 // (all matrices of the call, phase-ordered Gram -> square -> update). In the
 // fused mode one launch runs the whole step, and a square/update tile waits
 // (bounded, on a per-matrix counter) until every Gram/square tile of its
 // matrix has been stored.
+//
+// Symmetric outputs: only 32 x 32 chunks on or above the diagonal are
+// stored. Strictly-upper chunks are stored and mirrored; a diagonal chunk is
+// symmetrised from its upper half. The FP32 copy of A keeps the upper and
+// diagonal chunks only (the square epilogue reads nothing else).
 //
 // Split BF16 (BF16x3): every operand is x = hi + lo with hi = bf16(x),
 // lo = bf16(x - hi); each k-step issues hi*hi + hi*lo + lo*hi into the same
@@ -24,7 +37,6 @@
 
 #include <algorithm>
 #include <cstring>
-#include <numeric>
 #include <queue>
 #include <string>
 #include <vector>
@@ -35,20 +47,25 @@
 namespace pe {
 namespace {
 
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kThreads = 64 + kEpiThreads;
 constexpr int kBM = 128;        // UMMA M
+constexpr int kBN = 256;        // tile width (UMMA N, <= 256)
 constexpr int kBK = 64;         // k-block: one 128-byte swizzle row of BF16
-constexpr int kSymBN = 128;     // Gram / square tile width
-constexpr int kApplyBN = 256;   // update tile width
 constexpr int kTmemCols = 512;  // two 256-column accumulators
-constexpr int kMapsPerMat = 12;
-constexpr int kABytes = kBM * kBK * 2;        // 16 KB
-constexpr int kBBytes = kApplyBN * kBK * 2;   // 32 KB (max)
+constexpr int kABytes = kBM * kBK * 2;   // 16 KB
+constexpr int kBBytes = kBN * kBK * 2;   // 32 KB
+constexpr int kWarpStage = 10240;        // per epilogue warp staging (BF16 path)
 constexpr uint64_t kDefaultWaitNs = 1000000000ull;  // 1 s
 
 enum MapIdx {
-    kMapXK0 = 0, kMapXK1 = 1, kMapXM0 = 2, kMapXM1 = 3, kMapA = 4, kMapB = 5,
-    kLo = 6   // lo maps follow at +6
+    // operand maps, 128-byte swizzle: K-major boxes 64 x 128, MN-major 64 x 64
+    kMapXK0 = 0, kMapXK1, kMapXM0, kMapXM1, kMapA, kMapB,
+    kLo = 6,   // lo operand maps follow at +6 (BF16x3)
+    // epilogue maps, 32 x 32 boxes: FP32 with 128-byte swizzle, BF16 with 64-byte
+    kMapEXF = 12, kMapEXH0, kMapEXH1, kMapEAF, kMapEAH, kMapEBH, kMapEOut,
+    kMapsPerMat
 };
 
 struct StepArgs {
@@ -62,6 +79,7 @@ struct StepArgs {
     float a, b, c;
     int step, cur, last, dependent, withhold;
     uint64_t wait_ns;
+    long long* prof;    // optional per-CTA cycle counters (debug)
 };
 
 // ------------------------------------------------------------- PTX helpers
@@ -122,6 +140,22 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
             "r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13,
@@ -194,7 +228,7 @@ __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 // Bounded wait for a readiness counter (fused mode). On expiry the status
 // word records a timeout and the caller proceeds: the launch always ends,
@@ -214,11 +248,14 @@ __device__ void wait_counter(const int* cnt, int target, uint64_t limit, int* st
     }
 }
 
+// ------------------------------------------------------------ tile geometry
+
 struct Geo {
     int kind, mat, tm, tn, bn, nkb;
-    int mapA, mapB;      // hi maps
+    int mapA, mapB;      // hi operand maps
     int ya;              // A-operand row coordinate
     int b0;              // B-operand row (K-major) or column (MN-major) origin
+    int col0;            // first output column of the tile
 };
 
 __device__ __forceinline__ Geo tile_geo(const TileTask& tk, const DevMat& M, int cur) {
@@ -228,19 +265,18 @@ __device__ __forceinline__ Geo tile_geo(const TileTask& tk, const DevMat& M, int
     g.tm = tk.tm;
     g.tn = tk.tn;
     g.ya = tk.tm * kBM;
+    g.b0 = tk.tn * kBN;
+    g.col0 = g.b0;
     if (tk.kind == kGram) {
-        g.bn = kSymBN;
+        g.bn = min(kBN, M.sp - g.b0);
         g.nkb = M.Lp / kBK;
         g.mapA = g.mapB = cur ? kMapXK1 : kMapXK0;
-        g.b0 = tk.tn * kSymBN;
     } else if (tk.kind == kSquare) {
-        g.bn = kSymBN;
+        g.bn = min(kBN, M.sp - g.b0);
         g.nkb = M.sp / kBK;
         g.mapA = g.mapB = kMapA;
-        g.b0 = tk.tn * kSymBN;
     } else {
-        g.b0 = tk.tn * kApplyBN;
-        g.bn = min(kApplyBN, M.Lp - g.b0);
+        g.bn = min(kBN, M.Lp - g.b0);
         g.nkb = M.sp / kBK;
         g.mapA = kMapB;
         g.mapB = cur ? kMapXM1 : kMapXM0;
@@ -248,10 +284,20 @@ __device__ __forceinline__ Geo tile_geo(const TileTask& tk, const DevMat& M, int
     return g;
 }
 
-__device__ __forceinline__ void put_bf16(bf16* hi, bf16* lo, int64_t idx, float v) {
-    const bf16 h = __float2bfloat16_rn(v);
-    hi[idx] = h;
-    if (lo) lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+// chunk classes of a symmetric output
+enum { kChunkLower = 0, kChunkDiag = 1, kChunkUpper = 2 };
+
+__device__ __forceinline__ int chunk_class(int gi0, int gj0) {
+    if (gj0 + 32 <= gi0) return kChunkLower;
+    if (gj0 == gi0) return kChunkDiag;
+    return kChunkUpper;
+}
+
+// ------------------------------------------------------ epilogue helpers
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);   // a in the low half
+    return *reinterpret_cast<uint32_t*>(&h);
 }
 
 __device__ __forceinline__ void store_user(const DevMat& M, int i, int l, float v) {
@@ -261,63 +307,142 @@ __device__ __forceinline__ void store_user(const DevMat& M, int i, int l, float 
     else reinterpret_cast<float*>(M.user)[idx] = v;
 }
 
-// Epilogue of one 32-column chunk for TMEM lane (= tile row) r.
-template <int NS>
-__device__ __forceinline__ void epilogue_chunk(const Geo& g, const DevMat& M, const StepArgs& A, int r,
-                                               int col0, float (&v)[32]) {
-    const int gi = g.tm * kBM + r;
+// Swizzled 32 x 32 staging boxes. FP32 rows are 128 bytes (128-byte swizzle:
+// 16-byte chunk c of row r lives at chunk c ^ (r & 7)); BF16 rows are 64
+// bytes (64-byte swizzle: chunk c ^ ((r >> 1) & 3)). These are the layouts
+// the TMA engine reads and writes for the epilogue tensor maps.
+__device__ __forceinline__ uint32_t f32_off(int r, int c) {
+    return r * 128 + ((((c >> 2) ^ (r & 7)) & 7) << 4) + (c & 3) * 4;
+}
+__device__ __forceinline__ uint32_t bf16_off(int r, int c) {
+    return r * 64 + ((((c >> 3) ^ (r >> 1)) & 3) << 4) + (c & 7) * 2;
+}
+
+__device__ __forceinline__ void stage_f32_row(uint8_t* buf, int r, const float (&v)[32]) {
+#pragma unroll
+    for (int c4 = 0; c4 < 8; ++c4)
+        *reinterpret_cast<float4*>(buf + f32_off(r, 4 * c4)) =
+            make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
+}
+
+__device__ __forceinline__ void read_f32_row(const uint8_t* buf, int r, float (&v)[32]) {
+#pragma unroll
+    for (int c4 = 0; c4 < 8; ++c4) {
+        const float4 x = *reinterpret_cast<const float4*>(buf + f32_off(r, 4 * c4));
+        v[4 * c4] = x.x;
+        v[4 * c4 + 1] = x.y;
+        v[4 * c4 + 2] = x.z;
+        v[4 * c4 + 3] = x.w;
+    }
+}
+
+__device__ __forceinline__ void stage_bf16_row(uint8_t* buf, int r, const float (&v)[32]) {
+#pragma unroll
+    for (int c8 = 0; c8 < 4; ++c8) {
+        uint4 h;
+        h.x = pack_bf16x2(v[8 * c8 + 0], v[8 * c8 + 1]);
+        h.y = pack_bf16x2(v[8 * c8 + 2], v[8 * c8 + 3]);
+        h.z = pack_bf16x2(v[8 * c8 + 4], v[8 * c8 + 5]);
+        h.w = pack_bf16x2(v[8 * c8 + 6], v[8 * c8 + 7]);
+        *reinterpret_cast<uint4*>(buf + bf16_off(r, 8 * c8)) = h;
+    }
+}
+
+// transposed: element (c, r) of the box is v[c]
+__device__ __forceinline__ void stage_f32_col(uint8_t* buf, int r, const float (&v)[32]) {
+#pragma unroll
+    for (int c = 0; c < 32; ++c) *reinterpret_cast<float*>(buf + f32_off(c, r)) = v[c];
+}
+
+__device__ __forceinline__ void stage_bf16_col(uint8_t* buf, int r, const float (&v)[32]) {
+#pragma unroll
+    for (int c = 0; c < 32; ++c) *reinterpret_cast<bf16*>(buf + bf16_off(c, r)) = __float2bfloat16_rn(v[c]);
+}
+
+// symmetric box from the upper half held by row r: (r, c) for c >= r and (c, r) for c > r
+__device__ __forceinline__ void stage_f32_sym(uint8_t* buf, int r, const float (&v)[32]) {
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        if (c >= r) *reinterpret_cast<float*>(buf + f32_off(r, c)) = v[c];
+        if (c > r) *reinterpret_cast<float*>(buf + f32_off(c, r)) = v[c];
+    }
+}
+
+__device__ __forceinline__ void stage_bf16_sym(uint8_t* buf, int r, const float (&v)[32]) {
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        const bf16 h = __float2bfloat16_rn(v[c]);
+        if (c >= r) *reinterpret_cast<bf16*>(buf + bf16_off(r, c)) = h;
+        if (c > r) *reinterpret_cast<bf16*>(buf + bf16_off(c, r)) = h;
+    }
+}
+
+// ------------------------------------------ split-BF16 (register) epilogue
+
+__device__ __forceinline__ void put_hl(bf16* hi, bf16* lo, int64_t idx, float v) {
+    const bf16 h = __float2bfloat16_rn(v);
+    hi[idx] = h;
+    lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+__device__ __forceinline__ void store8_hl(bf16* hi, bf16* lo, const float* v) {
+    uint4 h, l;
+    float r[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) r[q] = v[q] - __bfloat162float(__float2bfloat16_rn(v[q]));
+    h.x = pack_bf16x2(v[0], v[1]);
+    h.y = pack_bf16x2(v[2], v[3]);
+    h.z = pack_bf16x2(v[4], v[5]);
+    h.w = pack_bf16x2(v[6], v[7]);
+    l.x = pack_bf16x2(r[0], r[1]);
+    l.y = pack_bf16x2(r[2], r[3]);
+    l.z = pack_bf16x2(r[4], r[5]);
+    l.w = pack_bf16x2(r[6], r[7]);
+    *reinterpret_cast<uint4*>(hi) = h;
+    *reinterpret_cast<uint4*>(lo) = l;
+}
+
+__device__ __forceinline__ void load32(float (&d)[32], const float* src) {
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(src + j);
+        d[j] = x.x;
+        d[j + 1] = x.y;
+        d[j + 2] = x.z;
+        d[j + 3] = x.w;
+    }
+}
+
+// One 32-column chunk of row gi for the split-BF16 path; cls is the chunk's
+// class for symmetric outputs.
+__device__ __forceinline__ void chunk_hl(const Geo& g, const DevMat& M, const StepArgs& A, int gi, int col0,
+                                         int cls, float (&v)[32], const float (&pre)[32]) {
     if (g.kind == kApply) {
         const int nxt = A.cur ^ 1;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = fmaf(A.a, pre[j], v[j]);
+        if (A.last) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) store_user(M, gi, col0 + j, v[j]);
+            return;
+        }
         float* xrow = M.xf + (int64_t)gi * M.Lp + col0;
 #pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-            const float4 x4 = *reinterpret_cast<const float4*>(xrow + j);
-            v[j + 0] = fmaf(A.a, x4.x, v[j + 0]);
-            v[j + 1] = fmaf(A.a, x4.y, v[j + 1]);
-            v[j + 2] = fmaf(A.a, x4.z, v[j + 2]);
-            v[j + 3] = fmaf(A.a, x4.w, v[j + 3]);
-        }
-        if (A.last) {
-#pragma unroll 4
-            for (int j = 0; j < 32; ++j) store_user(M, gi, col0 + j, v[j]);
-        } else {
+        for (int j = 0; j < 32; j += 4)
+            *reinterpret_cast<float4*>(xrow + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
 #pragma unroll
-            for (int j = 0; j < 32; j += 4)
-                *reinterpret_cast<float4*>(xrow + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-            bf16* hrow = M.xh[nxt] + (int64_t)gi * M.Lp + col0;
-            bf16* lrow = (NS == 3) ? M.xl[nxt] + (int64_t)gi * M.Lp + col0 : nullptr;
-#pragma unroll
-            for (int j = 0; j < 32; j += 8) {
-                __align__(16) bf16 h[8];
-                __align__(16) bf16 lo[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    h[q] = __float2bfloat16_rn(v[j + q]);
-                    if (NS == 3) lo[q] = __float2bfloat16_rn(v[j + q] - __bfloat162float(h[q]));
-                }
-                *reinterpret_cast<uint4*>(hrow + j) = *reinterpret_cast<const uint4*>(h);
-                if (NS == 3) *reinterpret_cast<uint4*>(lrow + j) = *reinterpret_cast<const uint4*>(lo);
-            }
-        }
+        for (int j = 0; j < 32; j += 8)
+            store8_hl(M.xh[nxt] + (int64_t)gi * M.Lp + col0 + j, M.xl[nxt] + (int64_t)gi * M.Lp + col0 + j, v + j);
         return;
     }
-    // symmetric kinds: Gram writes A (FP32 + BF16 [+ lo]); square writes B
     if (g.kind == kSquare) {
-        const float* arow = M.af + (int64_t)gi * M.sp + col0;
 #pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-            const float4 a4 = *reinterpret_cast<const float4*>(arow + j);
-            v[j + 0] = fmaf(A.b, a4.x, A.c * v[j + 0]);
-            v[j + 1] = fmaf(A.b, a4.y, A.c * v[j + 1]);
-            v[j + 2] = fmaf(A.b, a4.z, A.c * v[j + 2]);
-            v[j + 3] = fmaf(A.b, a4.w, A.c * v[j + 3]);
-        }
+        for (int j = 0; j < 32; ++j) v[j] = fmaf(A.b, pre[j], A.c * v[j]);
     }
     float* f32 = (g.kind == kGram) ? M.af : nullptr;
     bf16* hi = (g.kind == kGram) ? M.ah : M.bh;
-    bf16* lo = (NS == 3) ? ((g.kind == kGram) ? M.al : M.bl) : nullptr;
-    const bool diag = (g.tm == g.tn);
-    if (!diag) {
+    bf16* lo = (g.kind == kGram) ? M.al : M.bl;
+    if (cls == kChunkUpper) {
         if (f32) {
 #pragma unroll
             for (int j = 0; j < 32; j += 4)
@@ -325,51 +450,45 @@ __device__ __forceinline__ void epilogue_chunk(const Geo& g, const DevMat& M, co
                     make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         }
 #pragma unroll
-        for (int j = 0; j < 32; j += 8) {
-            __align__(16) bf16 h[8];
-            __align__(16) bf16 l8[8];
+        for (int j = 0; j < 32; j += 8)
+            store8_hl(hi + (int64_t)gi * M.sp + col0 + j, lo + (int64_t)gi * M.sp + col0 + j, v + j);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                h[q] = __float2bfloat16_rn(v[j + q]);
-                if (NS == 3) l8[q] = __float2bfloat16_rn(v[j + q] - __bfloat162float(h[q]));
-            }
-            *reinterpret_cast<uint4*>(hi + (int64_t)gi * M.sp + col0 + j) = *reinterpret_cast<const uint4*>(h);
-            if (NS == 3)
-                *reinterpret_cast<uint4*>(lo + (int64_t)gi * M.sp + col0 + j) = *reinterpret_cast<const uint4*>(l8);
-        }
-        // mirror: lanes hold consecutive rows, so each store is coalesced
-#pragma unroll 4
-        for (int j = 0; j < 32; ++j) {
-            const int64_t mi = (int64_t)(col0 + j) * M.sp + gi;
-            if (f32) f32[mi] = v[j];
-            put_bf16(hi, lo, mi, v[j]);
-        }
-    } else {
-#pragma unroll 4
+        for (int j = 0; j < 32; ++j) put_hl(hi, lo, (int64_t)(col0 + j) * M.sp + gi, v[j]);
+    } else {   // diagonal chunk: symmetrise from the upper half
+#pragma unroll
         for (int j = 0; j < 32; ++j) {
             const int gj = col0 + j;
             if (gj >= gi) {
                 const int64_t di = (int64_t)gi * M.sp + gj;
                 if (f32) f32[di] = v[j];
-                put_bf16(hi, lo, di, v[j]);
+                put_hl(hi, lo, di, v[j]);
             }
             if (gj > gi) {
                 const int64_t mi = (int64_t)gj * M.sp + gi;
                 if (f32) f32[mi] = v[j];
-                put_bf16(hi, lo, mi, v[j]);
+                put_hl(hi, lo, mi, v[j]);
             }
         }
     }
 }
 
+// -------------------------------------------------------------- kernel
+
 template <int NS>
 struct Cfg {
-    static constexpr int kStages = (NS == 1) ? 4 : 2;
-    // stage layout: A hi | [A lo] | B hi | [B lo]
-    static constexpr int kAOps = (NS == 1) ? 1 : 2;
+    static constexpr int kStages = (NS == 1) ? 3 : 2;
+    static constexpr int kAOps = (NS == 1) ? 1 : 2;   // stage: A hi | [A lo] | B hi | [B lo]
     static constexpr int kStage = kAOps * (kABytes + kBBytes);
-    static constexpr int kBarOff = kStages * kStage;
-    static constexpr size_t kSmem = 1024 + kBarOff + 256;
+    static constexpr int kEpiOff = kStages * kStage;
+    static constexpr int kBarOff = kEpiOff + ((NS == 1) ? kEpiWarps * kWarpStage : 0);
+    static constexpr size_t kSmem = 1024 + kBarOff + 512;
+};
+
+// Per-role cycle counters (debug profiling), slot k of CTA b at prof[16 b + k].
+enum ProfSlot {
+    kPTotal = 0, kPDepWait = 1, kPEmptyWait = 2, kPFullWait = 3, kPTEmptyWait = 4, kPTFullWait = 5,
+    kPGramBusy = 6, kPSquareBusy = 7, kPApplyBusy = 8, kPEpiDepWait = 9, kPTiles = 10, kPProducer = 11,
+    kPMma = 12
 };
 
 template <int NS>
@@ -383,12 +502,15 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
     uint64_t* tfull = empty + NST;
     uint64_t* tempty = tfull + 2;
     uint64_t* drain = tempty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* pfbar = drain + 1;            // one prefetch barrier per epilogue warp
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pfbar + kEpiWarps);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t limit = A.wait_ns ? A.wait_ns : kDefaultWaitNs;
     const int t_begin = A.off[blockIdx.x], t_end = A.off[blockIdx.x + 1];
+    long long* prof = A.prof ? A.prof + 16 * blockIdx.x : nullptr;
+    const long long k_t0 = clock64();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
@@ -397,12 +519,13 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&tfull[s], 1);
-            mbar_init(&tempty[s], 128);
+            mbar_init(&tempty[s], kEpiThreads);
         }
         mbar_init(drain, 1);
+        for (int w = 0; w < kEpiWarps; ++w) mbar_init(&pfbar[w], 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_async_smem();
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -421,21 +544,26 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
         uint32_t issued = 0;   // bit s: stage s has been issued at least once
         uint32_t last_par = 0; // bit s: parity of the last issue of stage s
         bool ok = true;
+        long long c_dep = 0, c_empty = 0;
         for (int it = t_begin; it < t_end && ok; ++it) {
             const TileTask tk = A.tiles[it];
             const DevMat& M = A.mats[tk.mat];
             const Geo g = tile_geo(tk, M, A.cur);
             const CUtensorMap* mp = A.maps + (size_t)tk.mat * kMapsPerMat;
             if (A.dependent && g.kind != kGram) {
+                const long long c0 = clock64();
                 const int which = (g.kind == kSquare) ? 0 : 1;
                 wait_counter(A.counters + 2 * g.mat + which, (A.step + 1) * A.need[2 * g.mat + which], limit,
                              A.status);
                 fence_proxy_async_global();
+                c_dep += clock64() - c0;
             }
             const uint32_t bbytes = (uint32_t)g.bn * kBK * 2;
             const uint32_t tx = (uint32_t)C::kAOps * (kABytes + bbytes);
             for (int kb = 0; kb < g.nkb; ++kb) {
+                const long long c0 = clock64();
                 if (!mbar_wait(&empty[stage], phase ^ 1, limit, abort_flag)) { ok = false; break; }
+                c_empty += clock64() - c0;
                 mbar_expect_tx(&full[stage], tx);
                 const uint32_t sbase = smem_u32(smem + stage * C::kStage);
                 const int kx = kb * kBK;
@@ -450,7 +578,9 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                             tma_load_2d(b_dst + j * (64 * kBK * 2), mp + g.mapB + lo_off, &full[stage],
                                         g.b0 + j * 64, kx);
                     } else {
-                        tma_load_2d(b_dst, mp + g.mapB + lo_off, &full[stage], kx, g.b0);
+                        for (int h = 0; h < g.bn / kBM; ++h)
+                            tma_load_2d(b_dst + h * kABytes, mp + g.mapB + lo_off, &full[stage], kx,
+                                        g.b0 + h * kBM);
                     }
                 }
                 issued |= 1u << stage;
@@ -465,6 +595,12 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             for (int s = 0; s < NST; ++s)
                 if (issued & (1u << s)) mbar_wait(&full[s], (last_par >> s) & 1u, limit, nullptr);
         }
+        if (prof) {
+            prof[kPDepWait] = c_dep;
+            prof[kPEmptyWait] = c_empty;
+            prof[kPProducer] = clock64() - k_t0;
+            prof[kPTiles] = t_end - t_begin;
+        }
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------------ MMA issuer
         int stage = 0;
@@ -472,17 +608,22 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
         int acc = 0;
         uint32_t acc_phase = 0;
         bool ok = true;
+        long long c_full = 0, c_tempty = 0;
         for (int it = t_begin; it < t_end && ok; ++it) {
             const TileTask tk = A.tiles[it];
             const DevMat& M = A.mats[tk.mat];
             const Geo g = tile_geo(tk, M, A.cur);
+            long long c0 = clock64();
             if (!mbar_wait(&tempty[acc], acc_phase ^ 1, limit, abort_flag)) { ok = false; break; }
+            c_tempty += clock64() - c0;
             tc_fence_after();
             const uint32_t d_tmem = tmem_base + acc * 256;
             const bool mn = (g.kind == kApply);
             const uint32_t idesc = idesc_bf16(kBM, g.bn, mn);
             for (int kb = 0; kb < g.nkb; ++kb) {
+                c0 = clock64();
                 if (!mbar_wait(&full[stage], phase, limit, abort_flag)) { ok = false; break; }
+                c_full += clock64() - c0;
                 tc_fence_after();
                 const uint32_t sbase = smem_u32(smem + stage * C::kStage);
 #pragma unroll
@@ -515,48 +656,199 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             umma_commit(drain);
             mbar_wait(drain, 0, limit, nullptr);
         }
+        if (prof) {
+            prof[kPFullWait] = c_full;
+            prof[kPTEmptyWait] = c_tempty;
+            prof[kPMma] = clock64() - k_t0;
+        }
     } else if (warp >= 2) {
         // ------------------------------------------------------ epilogue
-        const int q = warp & 3;            // TMEM lane quarter this warp may access
-        const int r = q * 32 + lane;       // tile row
-        const int etid = threadIdx.x - 64; // 0..127
+        const int ew = warp - 2;           // 0..7
+        const int q = warp & 3;            // TMEM lane quarter = the warp's 32 tile rows
+        const int grp = ew >> 2;           // column half of the tile
+        const int etid = threadIdx.x - 64; // 0..255
+        uint8_t* stg = smem + C::kEpiOff + ew * kWarpStage;
+        uint8_t* s_in = stg;               // FP32 operand prefetch / FP32 output (Gram)
+        uint8_t* s_out = stg + 4096;       // FP32 output (update), BF16 direct (symmetric)
+        uint8_t* s_h = stg + 8192;         // BF16 output (update); s_out + 2048: BF16 mirror
+        uint32_t pf_phase = 0;
         int acc = 0;
         uint32_t acc_phase = 0;
+        long long c_tfull = 0, c_dep = 0, c_gram = 0, c_sq = 0, c_ap = 0;
         for (int it = t_begin; it < t_end; ++it) {
             const TileTask tk = A.tiles[it];
             const DevMat& M = A.mats[tk.mat];
             const Geo g = tile_geo(tk, M, A.cur);
+            const CUtensorMap* mp = A.maps + (size_t)tk.mat * kMapsPerMat;
+            const int gi0 = g.tm * kBM + q * 32;    // the warp's first row
+            const int gi = gi0 + lane;
+            const int nch = g.bn / 64;              // 32-column chunks per warpgroup
+            const int cb = g.col0 + grp * nch * 32; // the warpgroup's first column
+            const bool sym = (g.kind != kApply);
+            const bool needs_in = (g.kind != kGram);
+            if (g.kind == kSquare && A.dependent) {   // A (FP32) comes from other CTAs
+                const long long c0 = clock64();
+                if (NS == 1) {
+                    if (lane == 0) {
+                        wait_counter(A.counters + 2 * g.mat, (A.step + 1) * A.need[2 * g.mat], limit, A.status);
+                        fence_proxy_async_global();
+                    }
+                    __syncwarp();
+                } else {
+                    wait_counter(A.counters + 2 * g.mat, (A.step + 1) * A.need[2 * g.mat], limit, A.status);
+                }
+                c_dep += clock64() - c0;
+            }
+            // first chunk that this warp stores (symmetric outputs skip lower chunks)
+            int first = 0;
+            if (sym) {
+                while (first < nch && chunk_class(gi0, cb + first * 32) == kChunkLower) ++first;
+            }
+            float pre[32];
+            const CUtensorMap* in_map = mp + ((g.kind == kApply) ? kMapEXF : kMapEAF);
+            const float* in_g = (g.kind == kApply) ? M.xf + (int64_t)gi * M.Lp : M.af + (int64_t)gi * M.sp;
+            if (NS == 1) {
+                if (needs_in && first < nch && lane == 0) {
+                    bulk_wait_read0();   // s_in may still feed the previous tile's store
+                    mbar_expect_tx(&pfbar[ew], 4096);
+                    tma_load_2d(smem_u32(s_in), in_map, &pfbar[ew], cb + first * 32, gi0);
+                }
+            } else if (needs_in && first < nch) {
+                load32(pre, in_g + cb + first * 32);
+            }
+            long long c0 = clock64();
             if (!mbar_wait(&tfull[acc], acc_phase, limit, abort_flag)) {
                 *abort_flag = 1;
                 atomicOr(A.status, 4);
                 break;
             }
             tc_fence_after();
-            if (A.dependent && g.kind == kSquare)   // A (FP32) comes from other CTAs
-                wait_counter(A.counters + 2 * g.mat, (A.step + 1) * A.need[2 * g.mat], limit, A.status);
-            const int nch = g.bn / 32;
-            const int colbase = (g.kind == kApply) ? g.tn * kApplyBN : g.tn * kSymBN;
-            for (int ch = 0; ch < nch; ++ch) {
+            const long long c1 = clock64();
+            c_tfull += c1 - c0;
+            const uint32_t tbase = tmem_base + acc * 256 + ((uint32_t)(q * 32) << 16) + grp * nch * 32;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (i >= nch || i < first) continue;
+                const int col0 = cb + i * 32;
+                const int cls = sym ? chunk_class(gi0, col0) : kChunkUpper;
+                if (cls == kChunkLower) continue;
+                // next stored chunk (for the prefetch)
+                int nx = i + 1;
+                if (sym)
+                    while (nx < nch && chunk_class(gi0, cb + nx * 32) == kChunkLower) ++nx;
                 float v[32];
-                tmem_ld32(tmem_base + acc * 256 + ((uint32_t)(q * 32) << 16) + ch * 32, v);
-                if (ch == nch - 1) {
-                    tc_fence_before();
-                    mbar_arrive(&tempty[acc]);
+                tmem_ld32(tbase + i * 32, v);
+                if (NS == 1) {
+                    if (needs_in) {
+                        mbar_wait(&pfbar[ew], pf_phase, limit, abort_flag);
+                        pf_phase ^= 1;
+                        read_f32_row(s_in, lane, pre);
+                    }
+                    // every lane has read the operand and the previous chunk's
+                    // stores have read their staging: refill and restage
+                    if (lane == 0) bulk_wait_read0();
+                    __syncwarp();
+                    if (needs_in && nx < nch && lane == 0) {
+                        mbar_expect_tx(&pfbar[ew], 4096);
+                        tma_load_2d(smem_u32(s_in), in_map, &pfbar[ew], cb + nx * 32, gi0);
+                    }
+                    if (g.kind == kApply) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = fmaf(A.a, pre[j], v[j]);
+                        if (!A.last) {
+                            stage_f32_row(s_out, lane, v);
+                            stage_bf16_row(s_h, lane, v);
+                            fence_async_smem();
+                            __syncwarp();
+                            if (lane == 0) {
+                                tma_store_2d(mp + kMapEXF, smem_u32(s_out), col0, gi0);
+                                tma_store_2d(mp + (A.cur ? kMapEXH0 : kMapEXH1), smem_u32(s_h), col0, gi0);
+                                bulk_commit();
+                            }
+                        } else if (M.out_tma) {
+                            uint8_t* o = (M.io == PE_IO_BF16) ? s_h : s_out;
+                            if (M.io == PE_IO_BF16) {
+                                if (M.trans) stage_bf16_col(o, lane, v); else stage_bf16_row(o, lane, v);
+                            } else {
+                                if (M.trans) stage_f32_col(o, lane, v); else stage_f32_row(o, lane, v);
+                            }
+                            fence_async_smem();
+                            __syncwarp();
+                            if (lane == 0) {
+                                if (M.trans) tma_store_2d(mp + kMapEOut, smem_u32(o), gi0, col0);
+                                else tma_store_2d(mp + kMapEOut, smem_u32(o), col0, gi0);
+                                bulk_commit();
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) store_user(M, gi, col0 + j, v[j]);
+                        }
+                    } else {
+                        if (g.kind == kSquare) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) v[j] = fmaf(A.b, pre[j], A.c * v[j]);
+                        }
+                        uint8_t* s_dir = s_out;
+                        uint8_t* s_mir = s_out + 2048;
+                        if (cls == kChunkDiag) {
+                            if (g.kind == kGram) stage_f32_sym(s_in, lane, v);
+                            stage_bf16_sym(s_dir, lane, v);
+                        } else {
+                            if (g.kind == kGram) stage_f32_row(s_in, lane, v);
+                            stage_bf16_row(s_dir, lane, v);
+                            stage_bf16_col(s_mir, lane, v);
+                        }
+                        fence_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            const CUtensorMap* hm = mp + ((g.kind == kGram) ? kMapEAH : kMapEBH);
+                            if (g.kind == kGram) tma_store_2d(mp + kMapEAF, smem_u32(s_in), col0, gi0);
+                            tma_store_2d(hm, smem_u32(s_dir), col0, gi0);
+                            if (cls != kChunkDiag) tma_store_2d(hm, smem_u32(s_mir), gi0, col0);
+                            bulk_commit();
+                        }
+                    }
+                } else {
+                    float nxt_pre[32];
+                    if (needs_in && nx < nch) load32(nxt_pre, in_g + cb + nx * 32);
+                    chunk_hl(g, M, A, gi, col0, cls, v, pre);
+                    if (needs_in && nx < nch) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) pre[j] = nxt_pre[j];
+                    }
                 }
-                epilogue_chunk<NS>(g, M, A, r, colbase + ch * 32, v);
             }
-            if (A.dependent && g.kind != kApply) {
+            tc_fence_before();
+            mbar_arrive(&tempty[acc]);
+            if (A.dependent && sym) {
+                if (NS == 1 && lane == 0) {
+                    bulk_wait0();
+                    fence_proxy_async_global();
+                }
                 __threadfence();
                 epi_bar();
                 if (etid == 0 && !(g.kind == kGram && g.mat == A.withhold))
                     red_release_add(A.counters + 2 * g.mat + (g.kind == kSquare ? 1 : 0), 1);
             }
+            const long long dc = clock64() - c1;
+            if (g.kind == kGram) c_gram += dc;
+            else if (g.kind == kSquare) c_sq += dc;
+            else c_ap += dc;
             acc ^= 1;
             if (acc == 0) acc_phase ^= 1;
+        }
+        if (NS == 1 && lane == 0) bulk_wait0();
+        if (prof && etid == 0) {
+            prof[kPTFullWait] = c_tfull;
+            prof[kPEpiDepWait] = c_dep;
+            prof[kPGramBusy] = c_gram;
+            prof[kPSquareBusy] = c_sq;
+            prof[kPApplyBusy] = c_ap;
         }
     }
     tc_fence_before();
     __syncthreads();
+    if (prof && threadIdx.x == 0) prof[kPTotal] = clock64() - k_t0;
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols));
@@ -583,16 +875,16 @@ EncodeTiledFn encode_fn(std::string* err) {
     return fn;
 }
 
-// BF16 row-major rows x cols (cols contiguous), box = box_cols x box_rows.
-bool make_map(EncodeTiledFn enc, CUtensorMap* m, const void* ptr, int rows, int cols, int box_rows,
-              int box_cols) {
+// 2-D row-major map: rows x cols, row pitch in bytes, box = box_cols x box_rows.
+bool make_map(EncodeTiledFn enc, CUtensorMap* m, const void* ptr, int64_t rows, int64_t cols, int64_t pitch,
+              int box_rows, int box_cols, bool f32, CUtensorMapSwizzle sw) {
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch};
     cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                     const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
@@ -601,17 +893,22 @@ struct HostTile {
     double cost;
 };
 
+// Tiles of one matrix. Symmetric products keep the 128 x 256 tiles that
+// reach the upper triangle (column end > row start).
 void tiles_of(const DevMat& M, int i, std::vector<HostTile>* ph) {
-    const int ts = M.sp / kBM;
-    for (int a = 0; a < ts; ++a)
-        for (int b = a; b < ts; ++b) {
-            ph[kGram].push_back(HostTile{TileTask{i, a, b, kGram}, (double)kBM * kSymBN * M.Lp});
-            ph[kSquare].push_back(HostTile{TileTask{i, a, b, kSquare}, (double)kBM * kSymBN * M.sp});
+    const int tm = M.sp / kBM;
+    const int ts = (M.sp + kBN - 1) / kBN;
+    for (int a = 0; a < tm; ++a)
+        for (int b = 0; b < ts; ++b) {
+            const int bn = std::min(kBN, M.sp - b * kBN);
+            if (b * kBN + bn <= a * kBM) continue;
+            ph[kGram].push_back(HostTile{TileTask{i, a, b, kGram}, (double)kBM * bn * M.Lp});
+            ph[kSquare].push_back(HostTile{TileTask{i, a, b, kSquare}, (double)kBM * bn * M.sp});
         }
-    const int tn = (M.Lp + kApplyBN - 1) / kApplyBN;
-    for (int a = 0; a < ts; ++a)
-        for (int b = 0; b < tn; ++b) {
-            const int bn = std::min(kApplyBN, M.Lp - b * kApplyBN);
+    const int tl = (M.Lp + kBN - 1) / kBN;
+    for (int a = 0; a < tm; ++a)
+        for (int b = 0; b < tl; ++b) {
+            const int bn = std::min(kBN, M.Lp - b * kBN);
             ph[kApply].push_back(HostTile{TileTask{i, a, b, kApply}, (double)kBM * bn * M.sp});
         }
 }
@@ -651,9 +948,10 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 size_t umma_workspace_bytes(const DevMat* mats, int count) {
     size_t tiles = 0;
     for (int i = 0; i < count; ++i) {
-        const int ts = mats[i].sp / kBM;
-        const int tn = (mats[i].Lp + kApplyBN - 1) / kApplyBN;
-        tiles += (size_t)ts * (ts + 1) + (size_t)ts * tn;
+        const size_t tm = mats[i].sp / kBM;
+        const size_t ts = (mats[i].sp + kBN - 1) / kBN;
+        const size_t tl = (mats[i].Lp + kBN - 1) / kBN;
+        tiles += 2 * tm * ts + tm * tl;
     }
     size_t b = 0;
     b += align_up(sizeof(CUtensorMap) * kMapsPerMat * count, 1024);
@@ -663,7 +961,7 @@ size_t umma_workspace_bytes(const DevMat* mats, int count) {
     return b + 4096;
 }
 
-int umma_build(UmmaPlan* P, const DevMat* mats, const DevMat* d_mats, int count, int dtype, int sms, char* ws,
+int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, int sms, char* ws,
                size_t ws_bytes, int* counters, bool tune, std::string* err) {
     (void)tune;
     EncodeTiledFn enc = encode_fn(err);
@@ -677,29 +975,50 @@ int umma_build(UmmaPlan* P, const DevMat* mats, const DevMat* d_mats, int count,
     memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
     std::vector<HostTile> ph[3];
     std::vector<int> need(2 * count);
+    const CUtensorMapSwizzle S128 = CU_TENSOR_MAP_SWIZZLE_128B, S64 = CU_TENSOR_MAP_SWIZZLE_64B;
     for (int i = 0; i < count; ++i) {
-        const DevMat& M = mats[i];
+        DevMat& M = mats[i];
         CUtensorMap* mp = maps.data() + (size_t)i * kMapsPerMat;
         bool ok = true;
+        const int64_t xp = (int64_t)M.Lp * 2, sp2 = (int64_t)M.sp * 2;
         for (int lo = 0; lo < (P->nsplit == 3 ? 2 : 1); ++lo) {
             bf16* const* x = lo ? M.xl : M.xh;
             const int o = lo ? kLo : 0;
-            ok &= make_map(enc, mp + o + kMapXK0, x[0], M.sp, M.Lp, kBM, kBK);
-            ok &= make_map(enc, mp + o + kMapXK1, x[1], M.sp, M.Lp, kBM, kBK);
-            ok &= make_map(enc, mp + o + kMapXM0, x[0], M.sp, M.Lp, kBK, 64);
-            ok &= make_map(enc, mp + o + kMapXM1, x[1], M.sp, M.Lp, kBK, 64);
-            ok &= make_map(enc, mp + o + kMapA, lo ? M.al : M.ah, M.sp, M.sp, kBM, kBK);
-            ok &= make_map(enc, mp + o + kMapB, lo ? M.bl : M.bh, M.sp, M.sp, kBM, kBK);
+            ok &= make_map(enc, mp + o + kMapXK0, x[0], M.sp, M.Lp, xp, kBM, kBK, false, S128);
+            ok &= make_map(enc, mp + o + kMapXK1, x[1], M.sp, M.Lp, xp, kBM, kBK, false, S128);
+            ok &= make_map(enc, mp + o + kMapXM0, x[0], M.sp, M.Lp, xp, kBK, 64, false, S128);
+            ok &= make_map(enc, mp + o + kMapXM1, x[1], M.sp, M.Lp, xp, kBK, 64, false, S128);
+            ok &= make_map(enc, mp + o + kMapA, lo ? M.al : M.ah, M.sp, M.sp, sp2, kBM, kBK, false, S128);
+            ok &= make_map(enc, mp + o + kMapB, lo ? M.bl : M.bh, M.sp, M.sp, sp2, kBM, kBK, false, S128);
+        }
+        if (P->nsplit == 1) {
+            ok &= make_map(enc, mp + kMapEXF, M.xf, M.sp, M.Lp, (int64_t)M.Lp * 4, 32, 32, true, S128);
+            ok &= make_map(enc, mp + kMapEXH0, M.xh[0], M.sp, M.Lp, xp, 32, 32, false, S64);
+            ok &= make_map(enc, mp + kMapEXH1, M.xh[1], M.sp, M.Lp, xp, 32, 32, false, S64);
+            ok &= make_map(enc, mp + kMapEAF, M.af, M.sp, M.sp, (int64_t)M.sp * 4, 32, 32, true, S128);
+            ok &= make_map(enc, mp + kMapEAH, M.ah, M.sp, M.sp, sp2, 32, 32, false, S64);
+            ok &= make_map(enc, mp + kMapEBH, M.bh, M.sp, M.sp, sp2, 32, 32, false, S64);
         }
         if (!ok) {
             *err = "cuTensorMapEncodeTiled failed for matrix " + std::to_string(i);
             return PE_ECUDA;
+        }
+        // the caller's buffer takes TMA stores when it is 16-byte aligned with
+        // a 16-byte multiple pitch
+        const int esz = (M.io == PE_IO_BF16) ? 2 : 4;
+        M.out_tma = 0;
+        if (P->nsplit == 1 && reinterpret_cast<uintptr_t>(M.user) % 16 == 0 && (M.ld * esz) % 16 == 0) {
+            M.out_tma = make_map(enc, mp + kMapEOut, M.user, M.m, M.n, M.ld * esz, 32, 32, esz == 4,
+                                 esz == 4 ? S128 : S64)
+                            ? 1
+                            : 0;
         }
         const size_t g0 = ph[kGram].size(), s0 = ph[kSquare].size();
         tiles_of(M, i, ph);
         need[2 * i] = (int)(ph[kGram].size() - g0);
         need[2 * i + 1] = (int)(ph[kSquare].size() - s0);
     }
+    cudaError_t e = cudaMemcpy(d_mats, mats, sizeof(DevMat) * count, cudaMemcpyHostToDevice);
     for (int k = 0; k < 3; ++k) sort_phase(ph[k]);
     std::vector<HostTile> fused;
     for (int k = 0; k < 3; ++k) fused.insert(fused.end(), ph[k].begin(), ph[k].end());
@@ -716,7 +1035,8 @@ int umma_build(UmmaPlan* P, const DevMat* mats, const DevMat* d_mats, int count,
     P->tiles = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (list.size() + 1), 256));
     P->tile_off = reinterpret_cast<int*>(take(sizeof(int) * (off.size()), 256));
     P->need = reinterpret_cast<int*>(take(sizeof(int) * 2 * count, 256));
-    cudaError_t e = cudaMemcpy(P->maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P->maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->tiles, list.data(), sizeof(TileTask) * list.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->tile_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->need, need.data(), sizeof(int) * need.size(), cudaMemcpyHostToDevice);
@@ -755,7 +1075,7 @@ int umma_build(UmmaPlan* P, const DevMat* mats, const DevMat* d_mats, int count,
     return PE_OK;
 }
 
-cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, bool phased, int withhold,
+cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, int phase, int withhold,
                       uint64_t wait_ns, int* status, cudaStream_t st, int* launched) {
     StepArgs A;
     A.mats = P->d_mats;
@@ -771,6 +1091,7 @@ cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, b
     A.last = last;
     A.withhold = withhold;
     A.wait_ns = wait_ns;
+    A.prof = reinterpret_cast<long long*>(P->prof);
     *launched = 0;
     auto go = [&](int grid, bool coop) -> cudaError_t {
         cudaLaunchConfig_t cfg;
@@ -788,21 +1109,17 @@ cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, b
         if (P->nsplit == 3) return cudaLaunchKernelEx(&cfg, umma_step_kernel<3>, A);
         return cudaLaunchKernelEx(&cfg, umma_step_kernel<1>, A);
     };
-    if (!phased) {
+    if (phase < 0) {
         A.off = P->tile_off;
         A.tiles = P->tiles;
         A.dependent = 1;
         return go(P->grid, true);
     }
     A.dependent = 0;
-    for (int k = 0; k < 3; ++k) {
-        if (!P->grid_phase[k]) continue;
-        A.off = P->ph_off[k];
-        A.tiles = P->ph_tiles[k];
-        cudaError_t e = go(P->grid_phase[k], false);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    if (!P->grid_phase[phase]) return cudaSuccess;
+    A.off = P->ph_off[phase];
+    A.tiles = P->ph_tiles[phase];
+    return go(P->grid_phase[phase], false);
 }
 
 }  // namespace pe

@@ -29,18 +29,21 @@ struct UmmaPlan {
     const DevMat* d_mats = nullptr;
     size_t smem_bytes = 0;
     int apply_bn = 256;
+    void* prof = nullptr;    // optional device buffer of 16 int64 per CTA (debug)
 };
 
 size_t umma_workspace_bytes(const DevMat* mats, int count);
 
 // Builds tensor maps and schedules inside `ws` (device memory of
-// umma_workspace_bytes()); d_mats already holds the descriptors.
-int umma_build(UmmaPlan* P, const DevMat* mats, const DevMat* d_mats, int count, int dtype, int sms,
+// umma_workspace_bytes()); sets DevMat::out_tma and re-uploads the
+// descriptors to d_mats.
+int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, int sms,
                char* ws, size_t ws_bytes, int* counters, bool tune, std::string* err);
 
-// Enqueue polynomial step t (0-based). Phased mode runs three grouped
-// launches; otherwise one persistent launch with per-matrix readiness waits.
-cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, bool phased,
+// Enqueue polynomial step t (0-based). phase < 0: one persistent launch of
+// the whole step with per-matrix readiness waits; phase 0/1/2: one grouped
+// launch of that product only (Gram, square, update).
+cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, int phase,
                       int withhold, uint64_t wait_ns, int* status, cudaStream_t st, int* launched);
 
 }  // namespace pe
