@@ -1,7 +1,9 @@
 // C ABI of the library: argument checks, workspace, cached plans (grouped
 // task lists, tensor maps, captured CUDA graphs) and the launch sequence of
 // the online stage (Alg. 1, online box):
-//   prepare (norm + scale + cast + transpose)  ->  T x [Gram -> A^2 -> update]
+//   prepare (one pass: cast + transpose + pad + Frobenius norm partials, last
+//   block computes the normalisation factors)  ->  T x [Gram -> A^2 -> update]
+//   (the first step applies the normalisation factor)
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -134,9 +136,9 @@ struct Plan {
     char* ws = nullptr;           // one allocation: descriptors, task lists, buffers
     size_t ws_bytes = 0;
     DevMat* d_mats = nullptr;
-    NormTask* d_norm = nullptr;
-    int n_norm = 0;
-    double* d_partials = nullptr;
+    double* d_partials = nullptr; // one per prepare tile
+    float* d_nscale = nullptr;    // per-matrix 1 / (scale ||G||_F + eps)
+    unsigned* d_ticket = nullptr; // prepare's last-block ticket
     TileTask* d_prep = nullptr;
     int n_prep = 0;
     TileTask* d_tiles[3] = {nullptr, nullptr, nullptr};   // SIMT per-phase lists
@@ -180,7 +182,6 @@ int build_plan(const PlanKey& key, Plan** out) {
     Carve cv;
     // layout of the single workspace allocation
     const size_t o_mats = cv.take(sizeof(DevMat) * count, 64);
-    std::vector<NormTask> norm;
     std::vector<TileTask> prep, tl[3];
     struct Off { size_t xf, xf2, xh0, xh1, xl0, xl1, af, ah, al, bfp, bh, bl; };
     std::vector<Off> offs(count);
@@ -199,15 +200,13 @@ int build_plan(const PlanKey& key, Plan** out) {
         M.L = (int32_t)std::max(m, n);
         M.sp = (int32_t)round_up(M.s, kPadS);
         M.Lp = (int32_t)round_up(M.L, kPadL);
-        const int rows_per = (int)std::max<int64_t>(1, 32768 / n);
         M.part0 = part;
-        for (int64_t r = 0; r < m; r += rows_per) {
-            norm.push_back(NormTask{i, (int32_t)r, (int32_t)std::min<int64_t>(m, r + rows_per), 0});
-            ++part;
-        }
-        M.npart = part - M.part0;
         for (int a = 0; a < M.sp / 64; ++a)
-            for (int b = 0; b < M.Lp / 64; ++b) prep.push_back(TileTask{i, a, b, -1});
+            for (int b = 0; b < M.Lp / 64; ++b) {
+                prep.push_back(TileTask{i, a, b, -1});
+                ++part;
+            }
+        M.npart = part - M.part0;
         const size_t sL = (size_t)M.sp * M.Lp, ss = (size_t)M.sp * M.sp;
         Off& o = offs[i];
         memset(&o, 0, sizeof(o));
@@ -240,10 +239,10 @@ int build_plan(const PlanKey& key, Plan** out) {
                 for (int b = 0; b < tL; ++b) tl[kApply].push_back(TileTask{i, a, b, kApply});
         }
     }
-    P->n_norm = (int)norm.size();
     P->n_prep = (int)prep.size();
-    const size_t o_norm = cv.take(sizeof(NormTask) * norm.size(), 64);
-    const size_t o_part = cv.take(sizeof(double) * norm.size(), 64);
+    const size_t o_part = cv.take(sizeof(double) * prep.size(), 64);
+    const size_t o_nscale = cv.take(sizeof(float) * count, 64);
+    const size_t o_ticket = cv.take(64, 64);
     const size_t o_prep = cv.take(sizeof(TileTask) * prep.size(), 64);
     size_t o_tl[3];
     for (int k = 0; k < 3; ++k) {
@@ -294,13 +293,14 @@ int build_plan(const PlanKey& key, Plan** out) {
         }
     }
     P->d_mats = reinterpret_cast<DevMat*>(base + o_mats);
-    P->d_norm = reinterpret_cast<NormTask*>(base + o_norm);
     P->d_partials = reinterpret_cast<double*>(base + o_part);
+    P->d_nscale = reinterpret_cast<float*>(base + o_nscale);
+    P->d_ticket = reinterpret_cast<unsigned*>(base + o_ticket);
     P->d_prep = reinterpret_cast<TileTask*>(base + o_prep);
     for (int k = 0; k < 3; ++k) P->d_tiles[k] = reinterpret_cast<TileTask*>(base + o_tl[k]);
     P->d_counters = reinterpret_cast<int*>(base + o_cnt);
     PE_CU(cudaMemcpy(P->d_mats, P->mats.data(), sizeof(DevMat) * count, cudaMemcpyHostToDevice));
-    PE_CU(cudaMemcpy(P->d_norm, norm.data(), sizeof(NormTask) * norm.size(), cudaMemcpyHostToDevice));
+    PE_CU(cudaMemset(P->d_ticket, 0, 64));
     PE_CU(cudaMemcpy(P->d_prep, prep.data(), sizeof(TileTask) * prep.size(), cudaMemcpyHostToDevice));
     for (int k = 0; k < 3; ++k)
         if (!tl[k].empty())
@@ -309,6 +309,7 @@ int build_plan(const PlanKey& key, Plan** out) {
     PE_CU(cudaMemset(P->d_counters, 0, sizeof(int) * P->n_counters));
     if (dtype != PE_FP32) {
         const bool tune = !(key.flags & PE_BATCH_NO_TUNE);
+        P->umma.nscale = P->d_nscale;
         int ust = umma_build(&P->umma, P->mats.data(), P->d_mats, count, dtype, P->ds->sms,
                              base + o_umma, umma_bytes, P->d_counters, tune, &g_err);
         if (ust != PE_OK) return ust;
@@ -325,14 +326,9 @@ int enqueue(Plan* P, cudaStream_t st) {
     if (k.dtype != PE_FP32) outputs |= kPrepBF16;
     if (k.dtype == PE_BF16X3) outputs |= kPrepBF16Lo;
     {
-        TraceScope ts(0, st);
-        PE_CU(launch_norm_partials(P->d_mats, P->d_norm, P->n_norm, P->d_partials, st));
-    }
-    ++nk;
-    {
         TraceScope ts(1, st);
-        PE_CU(launch_prepare(P->d_mats, P->d_prep, P->n_prep, P->d_partials, k.scale, k.eps, outputs,
-                             P->ds->status, P->d_counters, P->n_counters, st));
+        PE_CU(launch_prepare(P->d_mats, k.count, P->d_prep, P->n_prep, P->d_partials, k.scale, k.eps, outputs,
+                             P->d_nscale, P->ds->status, P->d_counters, P->n_counters, P->d_ticket, st));
     }
     ++nk;
     for (int t = 0; t < k.T; ++t) {
@@ -342,7 +338,7 @@ int enqueue(Plan* P, cudaStream_t st) {
             for (int ph = 0; ph < 3; ++ph) {
                 TraceScope ts(2 + ph, st);
                 PE_CU(launch_simt_phase(P->d_mats, P->d_tiles[ph], P->n_tiles[ph], ph, a, b, c, t & 1,
-                                        last, st));
+                                        last, t == 0, P->d_nscale, st));
                 ++nk;
             }
         } else {

@@ -38,7 +38,7 @@ struct DevMat {
     int32_t io;          // pe_io_type of the caller's buffer
     int32_t s, L;        // logical short / long side
     int32_t sp, Lp;      // padded sizes (multiples of kPadS / kPadL)
-    int32_t part0, npart;  // range of this matrix's norm partials
+    int32_t part0, npart;  // range of this matrix's prepare tiles (norm partials)
     int32_t out_tma;       // 1 when the caller's buffer admits TMA stores
     float* xf;           // FP32 X (master; updated in place on BF16 paths)
     float* xf2;          // FP32 ping-pong partner (FP32 path)
@@ -52,7 +52,6 @@ struct DevMat {
     bf16* bl;            // BF16 B lo (BF16x3)
 };
 
-struct NormTask { int32_t mat, row0, row1, pad; };
 struct TileTask { int32_t mat, tm, tn, kind; };  // kind: 0 Gram, 1 A^2, 2 update
 
 enum TileKind { kGram = 0, kSquare = 1, kApply = 2 };
@@ -61,13 +60,12 @@ enum TileKind { kGram = 0, kSquare = 1, kApply = 2 };
 enum PrepOut { kPrepF32 = 1, kPrepBF16 = 2, kPrepBF16Lo = 4 };
 
 // ---- launchers (return cudaError_t of the launch) ----
-cudaError_t launch_norm_partials(const DevMat* mats, const NormTask* tasks, int ntasks,
-                                 double* partials, cudaStream_t st);
-cudaError_t launch_prepare(const DevMat* mats, const TileTask* tiles, int ntiles, const double* partials,
-                           float scale, float eps, int outputs, int* status, int* counters,
-                           int ncounters, cudaStream_t st);
+cudaError_t launch_prepare(const DevMat* mats, int nmats, const TileTask* tiles, int ntiles, double* partials,
+                           float scale, float eps, int outputs, float* nscale, int* status, int* counters,
+                           int ncounters, unsigned* ticket, cudaStream_t st);
 cudaError_t launch_simt_phase(const DevMat* mats, const TileTask* tiles, int ntiles, int kind,
-                              float a, float b, float c, int src, int last, cudaStream_t st);
+                              float a, float b, float c, int src, int last, int first,
+                              const float* nscale, cudaStream_t st);
 
 }  // namespace pe
 #endif

@@ -1,13 +1,13 @@
 // Step S1 of the online stage (Alg. 1 online box; App. A online code):
 //   nu = ||G||_F,  X_0 = G / (scale * nu + eps),
-// written in the canonical short-side layout (X = G^T when m > n) and padded
-// with zeros to whole tiles, in every precision the chosen path needs.
-//
-// Two grouped launches cover all matrices of a call:
-//   pe_norm_partials  one block per row chunk, FP32 per thread, FP64 block sum
-//   pe_prepare        one block per 64 x 64 canonical tile; sums the matrix's
-//                     partials in a fixed order (deterministic), scales, casts,
-//                     transposes and zero-pads.
+// in one pass over G. Each block takes one 64 x 64 tile of the canonical
+// short-side layout (X = G^T when m > n), padded with zeros to whole tiles,
+// and writes it unscaled in every precision the chosen path needs, together
+// with the tile's sum of squares. The last block to finish (atomic ticket)
+// sums each matrix's tile partials in a fixed order and stores the matrix's
+// normalisation factor 1 / (scale * nu + eps); the first polynomial step
+// applies it (A = s^2 X X^T, X_1 = s (a X + B X)), which is the same map as
+// scaling X_0 first.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -23,49 +23,123 @@ __device__ __forceinline__ float load_in(const void* base, int io, int64_t idx) 
     return reinterpret_cast<const float*>(base)[idx];
 }
 
-__global__ void __launch_bounds__(256) norm_partials_kernel(const DevMat* __restrict__ mats,
-                                                            const NormTask* __restrict__ tasks,
-                                                            double* __restrict__ partials) {
-    const NormTask tk = tasks[blockIdx.x];
-    const DevMat& M = mats[tk.mat];
-    float acc = 0.f;
-    for (int r = tk.row0; r < tk.row1; ++r) {
-        const int64_t rb = (int64_t)r * M.ld;
-        for (int c = threadIdx.x; c < M.n; c += blockDim.x) {
-            const float v = load_in(M.user, M.io, rb + c);
-            acc = fmaf(v, v, acc);
+// four consecutive inputs of row `row` from column `col` (zero outside the matrix)
+__device__ __forceinline__ float4 load4(const DevMat& M, bool vec, int rows, int cols, int row, int col) {
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (row >= rows) return r;
+    const int64_t base = (int64_t)row * M.ld + col;
+    if (vec && col + 3 < cols) {
+        if (M.io == PE_IO_BF16) {
+            const uint2 u = *reinterpret_cast<const uint2*>(reinterpret_cast<const bf16*>(M.user) + base);
+            const __nv_bfloat162 p0 = *reinterpret_cast<const __nv_bfloat162*>(&u.x);
+            const __nv_bfloat162 p1 = *reinterpret_cast<const __nv_bfloat162*>(&u.y);
+            r = make_float4(__low2float(p0), __high2float(p0), __low2float(p1), __high2float(p1));
+        } else {
+            r = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(M.user) + base);
         }
+        return r;
     }
-    double d = (double)acc;
-    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-    __shared__ double red[8];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) red[w] = d;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-        partials[blockIdx.x] = s;
+    if (col + 0 < cols) r.x = load_in(M.user, M.io, base + 0);
+    if (col + 1 < cols) r.y = load_in(M.user, M.io, base + 1);
+    if (col + 2 < cols) r.z = load_in(M.user, M.io, base + 2);
+    if (col + 3 < cols) r.w = load_in(M.user, M.io, base + 3);
+    return r;
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ void put4(const DevMat& M, int outputs, int64_t o, float4 v) {
+    if (outputs & kPrepF32) *reinterpret_cast<float4*>(M.xf + o) = v;
+    if (outputs & (kPrepBF16 | kPrepBF16Lo)) {
+        uint2 h;
+        h.x = pack2(v.x, v.y);
+        h.y = pack2(v.z, v.w);
+        *reinterpret_cast<uint2*>(M.xh[0] + o) = h;
+        if (outputs & kPrepBF16Lo) {
+            const __nv_bfloat162 h0 = *reinterpret_cast<const __nv_bfloat162*>(&h.x);
+            const __nv_bfloat162 h1 = *reinterpret_cast<const __nv_bfloat162*>(&h.y);
+            uint2 l;
+            l.x = pack2(v.x - __low2float(h0), v.y - __high2float(h0));
+            l.y = pack2(v.z - __low2float(h1), v.w - __high2float(h1));
+            *reinterpret_cast<uint2*>(M.xl[0] + o) = l;
+        }
     }
 }
 
-__global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__ mats,
+__global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__ mats, int nmats,
                                                       const TileTask* __restrict__ tiles,
-                                                      const double* __restrict__ partials,
-                                                      float scale, float eps, int outputs,
-                                                      int* __restrict__ status,
-                                                      int* __restrict__ counters, int ncounters) {
+                                                      double* __restrict__ partials, float scale, float eps,
+                                                      int outputs, float* __restrict__ nscale,
+                                                      int* __restrict__ status, int* __restrict__ counters,
+                                                      int ncounters, unsigned* __restrict__ ticket) {
     __shared__ float tile[64][65];
-    __shared__ float s_inv;
+    __shared__ double red[8];
+    __shared__ int s_last;
     const TileTask tk = tiles[blockIdx.x];
     const DevMat& M = mats[tk.mat];
     if (blockIdx.x == 0) {
         for (int i = threadIdx.x; i < ncounters; i += blockDim.x) counters[i] = 0;
     }
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
+    const int i0 = tk.tm * 64, l0 = tk.tn * 64;
+    const int tid = threadIdx.x;
+    const int rr = tid >> 4, c4 = (tid & 15) * 4;   // 16 rows x 16 float4 per pass
+    const int esz = (M.io == PE_IO_BF16) ? 2 : 4;
+    const bool vec = (reinterpret_cast<uintptr_t>(M.user) % (4 * esz) == 0) && (M.ld % 4 == 0);
+    float ss = 0.f;
+    if (!M.trans) {
+        // X[i][l] = G[i][l]; G is s x L
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int r = rr + 16 * p;
+            const float4 v = load4(M, vec, M.s, M.L, i0 + r, l0 + c4);
+            ss = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, ss))));
+            put4(M, outputs, (int64_t)(i0 + r) * M.Lp + l0 + c4, v);
+        }
+    } else {
+        // X[i][l] = G[l][i]; G is L x s: read G rows l with i contiguous, transpose in smem
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int r = rr + 16 * p;
+            const float4 v = load4(M, vec, M.L, M.s, l0 + r, i0 + c4);
+            ss = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, ss))));
+            tile[r][c4 + 0] = v.x;
+            tile[r][c4 + 1] = v.y;
+            tile[r][c4 + 2] = v.z;
+            tile[r][c4 + 3] = v.w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int r = rr + 16 * p;   // canonical row i0 + r, columns l0 + c4 .. + 3
+            const float4 v = make_float4(tile[c4 + 0][r], tile[c4 + 1][r], tile[c4 + 2][r], tile[c4 + 3][r]);
+            put4(M, outputs, (int64_t)(i0 + r) * M.Lp + l0 + c4, v);
+        }
+    }
+    // tile sum of squares: FP32 per thread, FP64 across the block, fixed order
+    double d = (double)ss;
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if ((tid & 31) == 0) red[tid >> 5] = d;
+    __syncthreads();
+    if (tid == 0) {
         double s = 0.0;
-        for (int i = lane; i < M.npart; i += 32) s += partials[M.part0 + i];
+        for (int w = 0; w < 8; ++w) s += red[w];
+        partials[blockIdx.x] = s;
+        __threadfence();
+        const unsigned t = atomicAdd(ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    // last block: per-matrix normalisation factors
+    __threadfence();
+    const int w = tid >> 5, lane = tid & 31;
+    for (int m = w; m < nmats; m += 8) {
+        const DevMat& Mm = mats[m];
+        double s = 0.0;
+        for (int i = lane; i < Mm.npart; i += 32) s += *((volatile double*)&partials[Mm.part0 + i]);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
             const double nu = sqrt(s);
@@ -75,57 +149,20 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
                 atomicOr(status, 2);
                 inv = 0.f;
             }
-            s_inv = inv;
+            nscale[m] = inv;
         }
     }
     __syncthreads();
-    const float inv = s_inv;
-    const int i0 = tk.tm * 64, l0 = tk.tn * 64;
-    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 64 x 4
-    if (!M.trans) {
-        // X[i][l] = G[i][l]
-        for (int r = ty; r < 64; r += 4) {
-            const int i = i0 + r, l = l0 + tx;
-            float v = 0.f;
-            if (i < M.s && l < M.L) v = load_in(M.user, M.io, (int64_t)i * M.ld + l) * inv;
-            tile[r][tx] = v;
-        }
-    } else {
-        // X[i][l] = G[l][i]; read G rows l with i contiguous, transpose in smem
-        for (int r = ty; r < 64; r += 4) {
-            const int l = l0 + r, i = i0 + tx;
-            float v = 0.f;
-            if (i < M.s && l < M.L) v = load_in(M.user, M.io, (int64_t)l * M.ld + i) * inv;
-            tile[tx][r] = v;
-        }
-    }
-    __syncthreads();
-    for (int r = ty; r < 64; r += 4) {
-        const int i = i0 + r, l = l0 + tx;
-        const float v = tile[r][tx];
-        const int64_t o = (int64_t)i * M.Lp + l;
-        if (outputs & kPrepF32) M.xf[o] = v;
-        if (outputs & (kPrepBF16 | kPrepBF16Lo)) {
-            const bf16 h = __float2bfloat16_rn(v);
-            M.xh[0][o] = h;
-            if (outputs & kPrepBF16Lo) M.xl[0][o] = __float2bfloat16_rn(v - __bfloat162float(h));
-        }
-    }
+    if (tid == 0) *ticket = 0u;
 }
 
 }  // namespace
 
-cudaError_t launch_norm_partials(const DevMat* mats, const NormTask* tasks, int ntasks,
-                                 double* partials, cudaStream_t st) {
-    norm_partials_kernel<<<ntasks, 256, 0, st>>>(mats, tasks, partials);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_prepare(const DevMat* mats, const TileTask* tiles, int ntiles, const double* partials,
-                           float scale, float eps, int outputs, int* status, int* counters,
-                           int ncounters, cudaStream_t st) {
-    prepare_kernel<<<ntiles, 256, 0, st>>>(mats, tiles, partials, scale, eps, outputs, status,
-                                           counters, ncounters);
+cudaError_t launch_prepare(const DevMat* mats, int nmats, const TileTask* tiles, int ntiles, double* partials,
+                           float scale, float eps, int outputs, float* nscale, int* status, int* counters,
+                           int ncounters, unsigned* ticket, cudaStream_t st) {
+    prepare_kernel<<<ntiles, 256, 0, st>>>(mats, nmats, tiles, partials, scale, eps, outputs, nscale, status,
+                                           counters, ncounters, ticket);
     return cudaGetLastError();
 }
 

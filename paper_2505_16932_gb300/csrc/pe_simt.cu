@@ -81,7 +81,7 @@ template <int kKind>
 __global__ void __launch_bounds__(256) simt_phase_kernel(const DevMat* __restrict__ mats,
                                                          const TileTask* __restrict__ tiles,
                                                          float ca, float cb, float cc, int src,
-                                                         int last) {
+                                                         int last, int first, const float* __restrict__ nscale) {
     constexpr bool kBK = (kKind != kApply);
     __shared__ __align__(16) float As[2][BK][BM];
     __shared__ __align__(16) float Bs[2][BK][BN];
@@ -133,7 +133,9 @@ __global__ void __launch_bounds__(256) simt_phase_kernel(const DevMat* __restric
         __syncthreads();
     }
 
-    // epilogue
+    // epilogue; the first step applies the normalisation factor s
+    // (A = s^2 X X^T, X_1 = s (a X + B X)) to the unscaled prepared X
+    const float s0 = first ? nscale[tk.mat] : 1.f;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int r = r0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
@@ -144,6 +146,8 @@ __global__ void __launch_bounds__(256) simt_phase_kernel(const DevMat* __restric
 #pragma unroll
             for (int j = 0; j < 4; ++j) v[j] = acc[i][jh * 4 + j];
             if (kKind == kGram) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[j] *= s0 * s0;
                 *reinterpret_cast<float4*>(M.af + (int64_t)r * M.sp + c) = make_float4(v[0], v[1], v[2], v[3]);
                 if (tk.tm != tk.tn) {
 #pragma unroll
@@ -163,7 +167,7 @@ __global__ void __launch_bounds__(256) simt_phase_kernel(const DevMat* __restric
                 const float4 x4 = *reinterpret_cast<const float4*>(xs + (int64_t)r * M.Lp + c);
                 const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-                for (int j = 0; j < 4; ++j) v[j] = fmaf(ca, xv[j], v[j]);
+                for (int j = 0; j < 4; ++j) v[j] = s0 * fmaf(ca, xv[j], v[j]);
                 if (last) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) store_out(M, r, c + j, v[j]);
@@ -178,12 +182,19 @@ __global__ void __launch_bounds__(256) simt_phase_kernel(const DevMat* __restric
 }  // namespace
 
 cudaError_t launch_simt_phase(const DevMat* mats, const TileTask* tiles, int ntiles, int kind,
-                              float a, float b, float c, int src, int last, cudaStream_t st) {
+                              float a, float b, float c, int src, int last, int first,
+                              const float* nscale, cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
     switch (kind) {
-        case kGram: simt_phase_kernel<kGram><<<ntiles, 256, 0, st>>>(mats, tiles, a, b, c, src, last); break;
-        case kSquare: simt_phase_kernel<kSquare><<<ntiles, 256, 0, st>>>(mats, tiles, a, b, c, src, last); break;
-        default: simt_phase_kernel<kApply><<<ntiles, 256, 0, st>>>(mats, tiles, a, b, c, src, last); break;
+        case kGram:
+            simt_phase_kernel<kGram><<<ntiles, 256, 0, st>>>(mats, tiles, a, b, c, src, last, first, nscale);
+            break;
+        case kSquare:
+            simt_phase_kernel<kSquare><<<ntiles, 256, 0, st>>>(mats, tiles, a, b, c, src, last, first, nscale);
+            break;
+        default:
+            simt_phase_kernel<kApply><<<ntiles, 256, 0, st>>>(mats, tiles, a, b, c, src, last, first, nscale);
+            break;
     }
     return cudaGetLastError();
 }

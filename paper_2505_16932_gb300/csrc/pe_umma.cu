@@ -80,6 +80,7 @@ struct StepArgs {
     int step, cur, last, dependent, withhold;
     uint64_t wait_ns;
     long long* prof;    // optional per-CTA cycle counters (debug)
+    const float* nscale;  // per-matrix normalisation factor, applied in step 0
 };
 
 // ------------------------------------------------------------- PTX helpers
@@ -416,11 +417,11 @@ __device__ __forceinline__ void load32(float (&d)[32], const float* src) {
 // One 32-column chunk of row gi for the split-BF16 path; cls is the chunk's
 // class for symmetric outputs.
 __device__ __forceinline__ void chunk_hl(const Geo& g, const DevMat& M, const StepArgs& A, int gi, int col0,
-                                         int cls, float (&v)[32], const float (&pre)[32]) {
+                                         int cls, float s0, float (&v)[32], const float (&pre)[32]) {
     if (g.kind == kApply) {
         const int nxt = A.cur ^ 1;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = fmaf(A.a, pre[j], v[j]);
+        for (int j = 0; j < 32; ++j) v[j] = s0 * fmaf(A.a, pre[j], v[j]);
         if (A.last) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) store_user(M, gi, col0 + j, v[j]);
@@ -438,6 +439,9 @@ __device__ __forceinline__ void chunk_hl(const Geo& g, const DevMat& M, const St
     if (g.kind == kSquare) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = fmaf(A.b, pre[j], A.c * v[j]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] *= s0 * s0;
     }
     float* f32 = (g.kind == kGram) ? M.af : nullptr;
     bf16* hi = (g.kind == kGram) ? M.ah : M.bh;
@@ -686,6 +690,9 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             const int cb = g.col0 + grp * nch * 32; // the warpgroup's first column
             const bool sym = (g.kind != kApply);
             const bool needs_in = (g.kind != kGram);
+            // step 0 runs on the unscaled prepared X and applies the
+            // normalisation factor s: A = s^2 X X^T, X_1 = s (a X + B X)
+            const float s0 = (A.step == 0) ? A.nscale[g.mat] : 1.f;
             if (g.kind == kSquare && A.dependent) {   // A (FP32) comes from other CTAs
                 const long long c0 = clock64();
                 if (NS == 1) {
@@ -754,7 +761,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                     }
                     if (g.kind == kApply) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) v[j] = fmaf(A.a, pre[j], v[j]);
+                        for (int j = 0; j < 32; ++j) v[j] = s0 * fmaf(A.a, pre[j], v[j]);
                         if (!A.last) {
                             stage_f32_row(s_out, lane, v);
                             stage_bf16_row(s_h, lane, v);
@@ -787,6 +794,9 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                         if (g.kind == kSquare) {
 #pragma unroll
                             for (int j = 0; j < 32; ++j) v[j] = fmaf(A.b, pre[j], A.c * v[j]);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) v[j] *= s0 * s0;
                         }
                         uint8_t* s_dir = s_out;
                         uint8_t* s_mir = s_out + 2048;
@@ -811,7 +821,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                 } else {
                     float nxt_pre[32];
                     if (needs_in && nx < nch) load32(nxt_pre, in_g + cb + nx * 32);
-                    chunk_hl(g, M, A, gi, col0, cls, v, pre);
+                    chunk_hl(g, M, A, gi, col0, cls, s0, v, pre);
                     if (needs_in && nx < nch) {
 #pragma unroll
                         for (int j = 0; j < 32; ++j) pre[j] = nxt_pre[j];
@@ -1078,6 +1088,7 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
 cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, int phase, int withhold,
                       uint64_t wait_ns, int* status, cudaStream_t st, int* launched) {
     StepArgs A;
+    A.nscale = P->nscale;
     A.mats = P->d_mats;
     A.maps = reinterpret_cast<const CUtensorMap*>(P->maps);
     A.need = P->need;

@@ -30,6 +30,7 @@ struct UmmaPlan {
     size_t smem_bytes = 0;
     int apply_bn = 256;
     void* prof = nullptr;    // optional device buffer of 16 int64 per CTA (debug)
+    const float* nscale = nullptr;   // device: per-matrix normalisation factors
 };
 
 size_t umma_workspace_bytes(const DevMat* mats, int count);
