@@ -235,6 +235,45 @@ void pe_release(void);
  */
 int pe_debug_set(int key, int64_t value);
 
+/*
+ * pe_polar_noalloc -- pe_polar on the plain FP32 path (PE_FP32) for one
+ * matrix, for callers that must not have the library allocate device memory.
+ * The paper has no counterpart; this is a deployment variant of the same
+ * computation.
+ *
+ * Who needs it: code recorded into a CUDA graph in global capture mode (where
+ * cudaMalloc is not allowed), programs whose own allocator owns device memory
+ * up front (a framework's caching pool, a server with a fixed memory budget),
+ * and loops that cannot afford the implicit synchronisation of an allocation.
+ *
+ * Workspace: a file-scope device array of 32 MiB inside the library, present
+ * on every GPU where the library is loaded from load until process exit. The
+ * call needs (2 s'L' + 2 s'^2) * 4 bytes plus a few KiB of descriptors, with
+ * s' = min(m,n) and L' = max(m,n) rounded up to multiples of 128: e.g. every
+ * GPT-2-small Muon matrix (768 x 3072 and smaller), or 1024 x 2048. Larger
+ * matrices are rejected with PE_EINVAL and a message naming both sizes.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Sharing: all calls on a device use the same array, which keeps the last
+ * call's contents; each call reloads its descriptors and clears what must
+ * start at zero. Calls whose work overlaps on the GPU (different streams
+ * without ordering between them) race on the array and give wrong results:
+ * issue them on one stream or order the streams. The descriptors are staged
+ * with cudaMemcpyAsync from host memory, which orders the copy after work
+ * already queued on `stream`.
+ *
+ * First call on a device: looks up the array's device address with
+ * cudaGetSymbolAddress (which may load the module); make that first call
+ * before any stream capture that should contain later calls.
+ *
+ *   X, m, n, table, T, stream  as for pe_polar (X: m x n row-major FP32, ld = n,
+ *                              in/out, device memory).
+ * Errors: PE_EINVAL (arguments, or the matrix does not fit the workspace),
+ * PE_ECUDA. A non-finite input norm gives a non-finite output; there is no
+ * status word for this entry point.
+ */
+int pe_polar_noalloc(void* X, int64_t m, int64_t n, const double* table, int T, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

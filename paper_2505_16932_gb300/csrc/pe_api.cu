@@ -473,6 +473,9 @@ int run(void* const* X, const int64_t* m, const int64_t* n, const int64_t* ld, i
 }
 
 }  // namespace
+
+void set_last_error(const char* msg) { g_err = msg; }
+
 }  // namespace pe
 
 extern "C" {

@@ -14,6 +14,9 @@ constexpr int kMaxMatrices = 4096;
 constexpr int kPadS = 128;
 constexpr int kPadL = 128;
 
+// sets the thread-local message returned by pe_last_error()
+void set_last_error(const char* msg);
+
 // host FP64 coefficient solver (pe_coeffs.cpp)
 int coeffs_table(int degree, double l, int T, double safety, double cushion, unsigned flags,
                  double* coeffs, double* bounds, int* remez_iters, const char** why);
