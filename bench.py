@@ -174,9 +174,14 @@ def oracle_sample(wl, table, budget_s: float):
     flops = 0.0
     t0 = time.perf_counter()
     for G in wl.matrices:
-        O.polar_express(G, table)
+        # a matrix whose full iteration would overrun the budget (at an
+        # assumed 100 GFLOP/s FP64) is sampled with its first step only
+        steps = len(table)
+        if dense_equiv_flops([G.shape], steps) / 1e11 > max(budget_s, 1.0):
+            steps = 1
+        O.polar_express(G, table[:steps])
         done += 1
-        flops += algorithmic_flops([G.shape], len(table))
+        flops += algorithmic_flops([G.shape], steps)
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
@@ -261,6 +266,7 @@ def main():
     ap.add_argument("--phased", action="store_true", help="three grouped launches per step")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP32 comparison and accuracy sample")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-largest", action="store_true", help="skip the largest-configuration measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -409,6 +415,8 @@ def main():
     if rank == 0:
         if not args.no_extras:
             extras = accuracy_and_fp32(pe, torch, wl, table, dev_in, dtype, flush, stream, args)
+        if not args.no_largest and wl.name != "large_dense" and world == 1:
+            extras["largest_config"] = largest_config(pe, torch, flush, stream, min(args.steps, 10))
         tf, secs, done = oracle_sample(wl, table, args.cpu_budget)
         cpu = {"value": tf, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
                "sample": f"FP64 numpy oracle iteration of the first {done} of {len(shapes)} matrices, "
@@ -449,6 +457,83 @@ def main():
             "max_sigma_err_fp32": w32, "equal_error": bool(w16 <= 1.05 * w32 + 1e-4)}
     print(json.dumps(line))
     return 0
+
+
+def largest_config(pe, torch, flush, stream, steps):
+    """The largest configuration (8192 x 8192, 4096 x 14336, 14336 x 4096;
+    Haar U, V; s log-uniform in [1e-4, 1]; l = 1e-4, T = 6), generated on the
+    GPU with a seeded torch generator (input plumbing only). Times the BF16
+    grouped path and the FP32 plain path and compares their max|sigma - 1|
+    restricted to sigma_i(G) >= 1e-3 sigma_max (computed on the GPU from the
+    known factors: singular values of U1^T X V1)."""
+    shapes = [(8192, 8192), (4096, 14336), (14336, 4096)]
+    T, l = 6, 1e-4
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(3)
+    mats, facs = [], []
+    for m, n in shapes:
+        k = min(m, n)
+        U, _ = torch.linalg.qr(torch.randn(m, k, device="cuda", generator=gen))
+        V, _ = torch.linalg.qr(torch.randn(n, k, device="cuda", generator=gen))
+        e = torch.rand(k, device="cuda", generator=gen) * 4.0 - 4.0
+        sv = torch.sort(10.0 ** e, descending=True).values
+        mats.append(((U * sv) @ V.T).contiguous())
+        keep = sv >= 1e-3 * sv[0]
+        facs.append((U[:, keep].contiguous(), V[:, keep].contiguous()))
+    table = pe.pe_coeffs(5, l, T, 1.01)
+    flops = algorithmic_flops(shapes, T)
+    out = {"workload": "large_dense_8192sq_4096x14336_14336x4096", "T": T, "l": l, "flops_per_step": flops}
+    xs = [x.clone() for x in mats]
+
+    def timed(path, tab, n):
+        for _ in range(2):
+            for d, s0 in zip(xs, mats):
+                d.copy_(s0)
+            pe.pe_polar_batched(xs, tab, path)
+        tot = 0.0
+        for _ in range(n):
+            for d, s0 in zip(xs, mats):
+                d.copy_(s0)
+            flush.fill_(3.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pe.pe_polar_batched(xs, tab, path)
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / n
+
+    def restricted_err():
+        worst = 0.0
+        for X, (U1, V1) in zip(xs, facs):
+            C = U1.T @ X @ V1                  # FP32 (TF32 off)
+            sv = torch.linalg.svdvals(C)
+            worst = max(worst, float((sv - 1.0).abs().max()))
+        return worst
+
+    ms16 = timed("bf16", table, max(3, steps))
+    e16 = restricted_err()
+    ms32 = timed("fp32", table, 2)
+    e32 = restricted_err()
+    # smallest BF16 step count whose restricted error matches the FP32 one
+    t16, ms16_eq, e16_eq = T, ms16, e16
+    while e16_eq > 1.05 * e32 + 1e-4 and t16 < T + 4:
+        t16 += 1
+        tab16 = pe.pe_coeffs(5, l, t16, 1.01)
+        ms16_eq = timed("bf16", tab16, 3)
+        e16_eq = restricted_err()
+    peaks = measured_peaks()
+    out["bf16"] = {"value": flops / (ms16 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms16,
+                   "frac_of_bf16_peak": flops / (ms16 * 1e-3) / 1e12 / peaks["bf16_tflops"],
+                   "restricted_max_sigma_err": e16}
+    out["fp32_plain"] = {"value": flops / (ms32 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms32,
+                         "restricted_max_sigma_err": e32}
+    out["speedup_vs_fp32_plain_equal_err"] = {"value": ms32 / ms16_eq, "T_bf16": t16, "T_fp32": T,
+                                              "restricted_max_sigma_err_bf16": e16_eq,
+                                              "restricted_max_sigma_err_fp32": e32}
+    del xs, mats, facs
+    torch.cuda.empty_cache()
+    return out
 
 
 def accuracy_and_fp32(pe, torch, wl, table, dev_in, dtype, flush, stream, args):

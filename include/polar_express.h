@@ -231,6 +231,9 @@ void pe_release(void);
  *   key 4: device address of a buffer of 16 int64 per persistent CTA that
  *          tcgen05 launches fill with per-role cycle counters (0 disables;
  *          while set, calls enqueue directly, without a graph).
+ *   key 5: k-block (32 or 64) of tcgen05 plans built from now on (0 = default).
+ *   key 6: tile order (0 longest-first, 1 column-grouped raster) of tcgen05
+ *          plans built from now on (-1 = default).
  * Returns PE_EINVAL for an unknown key.
  */
 int pe_debug_set(int key, int64_t value);

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <list>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -32,6 +33,8 @@ int64_t g_dbg_withhold = -1;
 int64_t g_dbg_wait_ns = 0;
 bool g_dbg_fail_alloc = false;
 void* g_dbg_prof = nullptr;
+int g_dbg_bk = 0;      // 0: default k-block
+int g_dbg_order = -1;  // -1: default tile order
 
 // tracing: (kind, start, stop) event triples recorded on the call's stream
 struct TraceRec { int kind; cudaEvent_t a, b; };
@@ -308,8 +311,10 @@ int build_plan(const PlanKey& key, Plan** out) {
                              cudaMemcpyHostToDevice));
     PE_CU(cudaMemset(P->d_counters, 0, sizeof(int) * P->n_counters));
     if (dtype != PE_FP32) {
-        const bool tune = !(key.flags & PE_BATCH_NO_TUNE);
+        const bool tune = false;   // schedules are tuned after the plan is cached (autotune)
         P->umma.nscale = P->d_nscale;
+        if (g_dbg_bk == 32 || g_dbg_bk == 64) P->umma.bk = g_dbg_bk;
+        if (g_dbg_order >= 0) P->umma.order = g_dbg_order;
         int ust = umma_build(&P->umma, P->mats.data(), P->d_mats, count, dtype, P->ds->sms,
                              base + o_umma, umma_bytes, P->d_counters, tune, &g_err);
         if (ust != PE_OK) return ust;
@@ -318,8 +323,9 @@ int build_plan(const PlanKey& key, Plan** out) {
     return PE_OK;
 }
 
-// Enqueue the whole online stage of a plan on `st`.
-int enqueue(Plan* P, cudaStream_t st) {
+// Enqueue the whole online stage of a plan on `st`. With `tuning`, only the
+// first min(T, 3) steps run and none of them writes the caller's buffer.
+int enqueue(Plan* P, cudaStream_t st, bool tuning = false) {
     const PlanKey& k = P->key;
     int nk = 0;
     int outputs = kPrepF32;
@@ -331,9 +337,10 @@ int enqueue(Plan* P, cudaStream_t st) {
                              P->d_nscale, P->ds->status, P->d_counters, P->n_counters, P->d_ticket, st));
     }
     ++nk;
-    for (int t = 0; t < k.T; ++t) {
+    const int T = tuning ? std::min(k.T, 3) : k.T;
+    for (int t = 0; t < T; ++t) {
         const float a = k.coef[3 * t], b = k.coef[3 * t + 1], c = k.coef[3 * t + 2];
-        const int last = (t == k.T - 1);
+        const int last = (!tuning && t == k.T - 1);
         if (k.dtype == PE_FP32) {
             for (int ph = 0; ph < 3; ++ph) {
                 TraceScope ts(2 + ph, st);
@@ -364,8 +371,103 @@ int enqueue(Plan* P, cudaStream_t st) {
             nk += n_launched;
         }
     }
+    if (tuning) return PE_OK;
     g_dbg_withhold = -1;
     P->kernels_per_run = nk;
+    return PE_OK;
+}
+
+// ------------------------------------------------------------ autotuner
+// The tile schedule of a tcgen05 plan is picked by timing the candidate
+// schedules on the plan's own workspace (enqueue with `tuning`: the caller's
+// buffer is read by prepare but never written). Results are cached per
+// device and shape signature in memory and, when PE_AUTOTUNE_CACHE names a
+// file, in that file as JSON lines {"key": "...", "order": n}.
+
+std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_key(const PlanKey& k, const DeviceState* ds) {
+    std::string s = "sm" + std::to_string(ds->major) + std::to_string(ds->minor) + "x" + std::to_string(ds->sms) +
+                    "|d" + std::to_string(k.dtype) + "|T" + std::to_string(std::min(k.T, 3)) + "|";
+    for (int i = 0; i < k.count; ++i) {
+        const int64_t m = k.dims[3 * i], n = k.dims[3 * i + 1];
+        s += std::to_string(std::min(m, n)) + "x" + std::to_string(std::max(m, n)) + ",";
+    }
+    if (s.size() > 512) {   // long signatures are hashed
+        uint64_t h = 1469598103934665603ull;
+        for (unsigned char c : s) h = (h ^ c) * 1099511628211ull;
+        s = s.substr(0, 64) + "#" + std::to_string(h);
+    }
+    return s;
+}
+
+void tune_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = getenv("PE_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    char line[2048];
+    while (fgets(line, sizeof(line), f)) {
+        const char* k = strstr(line, "\"key\": \"");
+        const char* o = strstr(line, "\"order\": ");
+        if (!k || !o) continue;
+        k += 8;
+        const char* ke = strchr(k, '"');
+        if (!ke) continue;
+        g_tune[std::string(k, ke - k)] = atoi(o + 9);
+    }
+    fclose(f);
+}
+
+void tune_store(const std::string& key, int order) {
+    g_tune[key] = order;
+    const char* path = getenv("PE_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "{\"key\": \"%s\", \"order\": %d}\n", key.c_str(), order);
+    fclose(f);
+}
+
+int autotune(Plan* P, cudaStream_t st) {
+    tune_load();
+    const std::string key = tune_key(P->key, P->ds);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+        if (it->second != P->umma.order) return umma_schedule(&P->umma, it->second, &g_err);
+        return PE_OK;
+    }
+    cudaEvent_t a = nullptr, b = nullptr;
+    PE_CU(cudaEventCreate(&a));
+    PE_CU(cudaEventCreate(&b));
+    PE_CU(cudaStreamSynchronize(st));
+    float best = 1e30f;
+    int best_order = P->umma.order;
+    int r = PE_OK;
+    for (int order = 0; order < 2 && r == PE_OK; ++order) {
+        r = umma_schedule(&P->umma, order, &g_err);
+        if (r != PE_OK) break;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && r == PE_OK; ++rep) {   // warm-up, then timed
+            cudaEventRecord(a, st);
+            r = enqueue(P, st, true);
+            cudaEventRecord(b, st);
+            if (cudaEventSynchronize(b) != cudaSuccess) r = cuda_fail(cudaGetLastError(), "autotune");
+            cudaEventElapsedTime(&ms, a, b);
+        }
+        if (r == PE_OK && ms < best) {
+            best = ms;
+            best_order = order;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (r != PE_OK) return r;
+    tune_store(key, best_order);
+    if (best_order != P->umma.order) return umma_schedule(&P->umma, best_order, &g_err);
     return PE_OK;
 }
 
@@ -442,6 +544,10 @@ int run(void* const* X, const int64_t* m, const int64_t* n, const int64_t* ld, i
     bool fresh = false;
     int r = get_plan(key, st, &P, &fresh);
     if (r != PE_OK) return r;
+    if (fresh && dtype != PE_FP32 && !(flags & PE_BATCH_NO_TUNE) && g_dbg_order < 0) {
+        r = autotune(P, st);
+        if (r != PE_OK) return r;
+    }
     const bool use_graph = !(flags & PE_BATCH_NO_GRAPH) && count > 1;
     if (!use_graph || g_dbg_withhold >= 0 || g_trace || g_dbg_prof) {
         r = enqueue(P, st);
@@ -583,6 +689,8 @@ int pe_debug_set(int key, int64_t value) {
         case 2: pe::g_dbg_wait_ns = value < 0 ? 0 : value; return PE_OK;
         case 3: pe::g_dbg_fail_alloc = value != 0; return PE_OK;
         case 4: pe::g_dbg_prof = reinterpret_cast<void*>(value); return PE_OK;
+        case 5: pe::g_dbg_bk = (int)value; return PE_OK;
+        case 6: pe::g_dbg_order = (int)value; return PE_OK;
         default: return pe::fail(PE_EINVAL, "unknown debug key");
     }
 }

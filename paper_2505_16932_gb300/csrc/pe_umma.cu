@@ -52,10 +52,10 @@ constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kEpiThreads;
 constexpr int kBM = 128;        // UMMA M
 constexpr int kBN = 256;        // tile width (UMMA N, <= 256)
-constexpr int kBK = 64;         // k-block: one 128-byte swizzle row of BF16
 constexpr int kTmemCols = 512;  // two 256-column accumulators
-constexpr int kABytes = kBM * kBK * 2;   // 16 KB
-constexpr int kBBytes = kBN * kBK * 2;   // 32 KB
+// The k-block BK (64 or 32 BF16 elements: one 128- or 64-byte swizzle row)
+// is a template parameter; a smaller k-block gives more, smaller pipeline
+// stages in the same shared memory.
 constexpr int kWarpStage = 10240;        // per epilogue warp staging (BF16 path)
 constexpr uint64_t kDefaultWaitNs = 1000000000ull;  // 1 s
 
@@ -162,10 +162,10 @@ __device__ __forceinline__ void fence_async_smem() {
 // Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13,
 // leading-dimension byte offset >> 4 in 16-29, stride-dimension byte offset
 // >> 4 in 32-45, descriptor version 1 in bits 46-47, swizzle mode in 61-63
-// (2 = 128-byte swizzle).
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// (2 = 128-byte swizzle, 4 = 64-byte swizzle).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t swz) {
     return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)swz << 61);
 }
 
 // Instruction descriptor, kind::f16: D format F32 (bits 4-5 = 1), A and B
@@ -259,6 +259,7 @@ struct Geo {
     int col0;            // first output column of the tile
 };
 
+template <int BK>
 __device__ __forceinline__ Geo tile_geo(const TileTask& tk, const DevMat& M, int cur) {
     Geo g;
     g.kind = tk.kind;
@@ -270,15 +271,15 @@ __device__ __forceinline__ Geo tile_geo(const TileTask& tk, const DevMat& M, int
     g.col0 = g.b0;
     if (tk.kind == kGram) {
         g.bn = min(kBN, M.sp - g.b0);
-        g.nkb = M.Lp / kBK;
+        g.nkb = M.Lp / BK;
         g.mapA = g.mapB = cur ? kMapXK1 : kMapXK0;
     } else if (tk.kind == kSquare) {
         g.bn = min(kBN, M.sp - g.b0);
-        g.nkb = M.sp / kBK;
+        g.nkb = M.sp / BK;
         g.mapA = g.mapB = kMapA;
     } else {
         g.bn = min(kBN, M.Lp - g.b0);
-        g.nkb = M.sp / kBK;
+        g.nkb = M.sp / BK;
         g.mapA = kMapB;
         g.mapB = cur ? kMapXM1 : kMapXM0;
     }
@@ -478,11 +479,15 @@ __device__ __forceinline__ void chunk_hl(const Geo& g, const DevMat& M, const St
 
 // -------------------------------------------------------------- kernel
 
-template <int NS>
+template <int NS, int BK>
 struct Cfg {
-    static constexpr int kStages = (NS == 1) ? 3 : 2;
+    static constexpr int kABytes = kBM * BK * 2;      // A tile of one k-block
+    static constexpr int kBBytes = kBN * BK * 2;      // B tile of one k-block
     static constexpr int kAOps = (NS == 1) ? 1 : 2;   // stage: A hi | [A lo] | B hi | [B lo]
     static constexpr int kStage = kAOps * (kABytes + kBBytes);
+    static constexpr int kStages = ((NS == 1) ? 3 : 2) * (64 / BK);
+    static constexpr uint32_t kSwzK = (BK == 64) ? 2u : 4u;   // K-major operand swizzle
+    static constexpr uint32_t kSboK = 8 * BK * 2;             // 8 rows of one k-block
     static constexpr int kEpiOff = kStages * kStage;
     static constexpr int kBarOff = kEpiOff + ((NS == 1) ? kEpiWarps * kWarpStage : 0);
     static constexpr size_t kSmem = 1024 + kBarOff + 512;
@@ -495,9 +500,11 @@ enum ProfSlot {
     kPMma = 12
 };
 
-template <int NS>
+template <int NS, int BK>
 __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_constant__ StepArgs A) {
-    using C = Cfg<NS>;
+    using C = Cfg<NS, BK>;
+    constexpr int kABytes = C::kABytes;
+    constexpr int kBBytes = C::kBBytes;
     constexpr int NST = C::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -552,7 +559,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
         for (int it = t_begin; it < t_end && ok; ++it) {
             const TileTask tk = A.tiles[it];
             const DevMat& M = A.mats[tk.mat];
-            const Geo g = tile_geo(tk, M, A.cur);
+            const Geo g = tile_geo<BK>(tk, M, A.cur);
             const CUtensorMap* mp = A.maps + (size_t)tk.mat * kMapsPerMat;
             if (A.dependent && g.kind != kGram) {
                 const long long c0 = clock64();
@@ -562,7 +569,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                 fence_proxy_async_global();
                 c_dep += clock64() - c0;
             }
-            const uint32_t bbytes = (uint32_t)g.bn * kBK * 2;
+            const uint32_t bbytes = (uint32_t)g.bn * BK * 2;
             const uint32_t tx = (uint32_t)C::kAOps * (kABytes + bbytes);
             for (int kb = 0; kb < g.nkb; ++kb) {
                 const long long c0 = clock64();
@@ -570,7 +577,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                 c_empty += clock64() - c0;
                 mbar_expect_tx(&full[stage], tx);
                 const uint32_t sbase = smem_u32(smem + stage * C::kStage);
-                const int kx = kb * kBK;
+                const int kx = kb * BK;
 #pragma unroll
                 for (int o = 0; o < C::kAOps; ++o) {
                     const int lo_off = o ? kLo : 0;
@@ -579,7 +586,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                     tma_load_2d(a_dst, mp + g.mapA + lo_off, &full[stage], kx, g.ya);
                     if (g.kind == kApply) {
                         for (int j = 0; j < g.bn / 64; ++j)
-                            tma_load_2d(b_dst + j * (64 * kBK * 2), mp + g.mapB + lo_off, &full[stage],
+                            tma_load_2d(b_dst + j * (64 * BK * 2), mp + g.mapB + lo_off, &full[stage],
                                         g.b0 + j * 64, kx);
                     } else {
                         for (int h = 0; h < g.bn / kBM; ++h)
@@ -616,7 +623,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
         for (int it = t_begin; it < t_end && ok; ++it) {
             const TileTask tk = A.tiles[it];
             const DevMat& M = A.mats[tk.mat];
-            const Geo g = tile_geo(tk, M, A.cur);
+            const Geo g = tile_geo<BK>(tk, M, A.cur);
             long long c0 = clock64();
             if (!mbar_wait(&tempty[acc], acc_phase ^ 1, limit, abort_flag)) { ok = false; break; }
             c_tempty += clock64() - c0;
@@ -631,18 +638,18 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                 tc_fence_after();
                 const uint32_t sbase = smem_u32(smem + stage * C::kStage);
 #pragma unroll
-                for (int kk = 0; kk < kBK / 16; ++kk) {
+                for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
                     for (int p = 0; p < (NS == 1 ? 1 : 3); ++p) {
                         // products: hi*hi, hi*lo, lo*hi
                         const int ao = (p == 2) ? 1 : 0;
                         const int bo = (p == 1) ? 1 : 0;
                         const uint32_t a_addr = sbase + ao * kABytes + kk * 32;
-                        const uint64_t adesc = sdesc(a_addr, 16, 1024);
+                        const uint64_t adesc = sdesc(a_addr, 16, C::kSboK, C::kSwzK);
                         const uint32_t b_base = sbase + C::kAOps * kABytes + bo * kBBytes;
                         uint64_t bdesc;
-                        if (mn) bdesc = sdesc(b_base + kk * 16 * 128, 64 * kBK * 2, 1024);
-                        else bdesc = sdesc(b_base + kk * 32, 16, 1024);
+                        if (mn) bdesc = sdesc(b_base + kk * 16 * 128, 64 * BK * 2, 1024, 2u);
+                        else bdesc = sdesc(b_base + kk * 32, 16, C::kSboK, C::kSwzK);
                         umma_bf16(d_tmem, adesc, bdesc, idesc, (kb | kk | p) != 0);
                     }
                 }
@@ -682,7 +689,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
         for (int it = t_begin; it < t_end; ++it) {
             const TileTask tk = A.tiles[it];
             const DevMat& M = A.mats[tk.mat];
-            const Geo g = tile_geo(tk, M, A.cur);
+            const Geo g = tile_geo<BK>(tk, M, A.cur);
             const CUtensorMap* mp = A.maps + (size_t)tk.mat * kMapsPerMat;
             const int gi0 = g.tm * kBM + q * 32;    // the warp's first row
             const int gi = gi0 + lane;
@@ -947,13 +954,63 @@ void lpt_assign(const std::vector<HostTile>& order, int grid, std::vector<int>* 
     (*off)[grid] = (int)out->size();
 }
 
-void sort_phase(std::vector<HostTile>& v) {
-    std::stable_sort(v.begin(), v.end(), [](const HostTile& x, const HostTile& y) { return x.cost > y.cost; });
+// Tile order inside a phase. Mode 0: longest first. Mode 1: by matrix
+// (largest first), then in column groups of 8 tile columns, row-major inside
+// a group, so that the tiles running at one time share few operand blocks.
+void sort_phase(std::vector<HostTile>& v, int mode, const std::vector<double>& mat_cost) {
+    if (mode == 0) {
+        std::stable_sort(v.begin(), v.end(), [](const HostTile& x, const HostTile& y) { return x.cost > y.cost; });
+        return;
+    }
+    std::stable_sort(v.begin(), v.end(), [&](const HostTile& x, const HostTile& y) {
+        if (x.t.mat != y.t.mat) {
+            const double cx = mat_cost[x.t.mat], cy = mat_cost[y.t.mat];
+            if (cx != cy) return cx > cy;
+            return x.t.mat < y.t.mat;
+        }
+        if (x.t.tn / 8 != y.t.tn / 8) return x.t.tn / 8 < y.t.tn / 8;
+        if (x.t.tm != y.t.tm) return x.t.tm < y.t.tm;
+        return x.t.tn < y.t.tn;
+    });
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
+
+int umma_schedule(UmmaPlan* P, int order, std::string* err) {
+    const int sms = P->sms;
+    std::vector<HostTile> ph[3];
+    for (int k = 0; k < 3; ++k) {
+        for (size_t i = 0; i < P->ph_t[k].size(); ++i) ph[k].push_back(HostTile{P->ph_t[k][i], P->ph_c[k][i]});
+        sort_phase(ph[k], order, P->mat_cost);
+    }
+    std::vector<HostTile> fused;
+    for (int k = 0; k < 3; ++k) fused.insert(fused.end(), ph[k].begin(), ph[k].end());
+    P->ntiles = (int)fused.size();
+    P->grid = std::max(1, std::min(sms, P->ntiles));
+    std::vector<int> off;
+    std::vector<TileTask> list;
+    lpt_assign(fused, P->grid, &off, &list);
+    cudaError_t e = cudaMemcpy(P->tiles, list.data(), sizeof(TileTask) * list.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->tile_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        std::vector<int> poff;
+        std::vector<TileTask> plist;
+        const int g = std::max(1, std::min(sms, (int)ph[k].size()));
+        lpt_assign(ph[k], g, &poff, &plist);
+        P->grid_phase[k] = ph[k].empty() ? 0 : g;
+        if (!plist.empty())
+            e = cudaMemcpy(P->ph_tiles[k], plist.data(), sizeof(TileTask) * plist.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(P->ph_off[k], poff.data(), sizeof(int) * poff.size(), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        *err = std::string("uploading the tile schedule: ") + cudaGetErrorString(e);
+        return PE_ECUDA;
+    }
+    P->order = order;
+    return PE_OK;
+}
 
 size_t umma_workspace_bytes(const DevMat* mats, int count) {
     size_t tiles = 0;
@@ -966,7 +1023,7 @@ size_t umma_workspace_bytes(const DevMat* mats, int count) {
     size_t b = 0;
     b += align_up(sizeof(CUtensorMap) * kMapsPerMat * count, 1024);
     b += 2 * align_up(sizeof(TileTask) * (tiles + 1), 256);   // fused + phased lists
-    b += 4 * align_up(sizeof(int) * (1024 + 1), 256);         // CSR offsets
+    b += 4 * align_up(sizeof(int) * (4096 + 1), 256);         // CSR offsets (grid <= 4096)
     b += align_up(sizeof(int) * 2 * count, 256);
     return b + 4096;
 }
@@ -991,15 +1048,17 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
         CUtensorMap* mp = maps.data() + (size_t)i * kMapsPerMat;
         bool ok = true;
         const int64_t xp = (int64_t)M.Lp * 2, sp2 = (int64_t)M.sp * 2;
+        const int bk = P->bk;
+        const CUtensorMapSwizzle SK = (bk == 64) ? S128 : S64;   // K-major operand boxes: bk x 128
         for (int lo = 0; lo < (P->nsplit == 3 ? 2 : 1); ++lo) {
             bf16* const* x = lo ? M.xl : M.xh;
             const int o = lo ? kLo : 0;
-            ok &= make_map(enc, mp + o + kMapXK0, x[0], M.sp, M.Lp, xp, kBM, kBK, false, S128);
-            ok &= make_map(enc, mp + o + kMapXK1, x[1], M.sp, M.Lp, xp, kBM, kBK, false, S128);
-            ok &= make_map(enc, mp + o + kMapXM0, x[0], M.sp, M.Lp, xp, kBK, 64, false, S128);
-            ok &= make_map(enc, mp + o + kMapXM1, x[1], M.sp, M.Lp, xp, kBK, 64, false, S128);
-            ok &= make_map(enc, mp + o + kMapA, lo ? M.al : M.ah, M.sp, M.sp, sp2, kBM, kBK, false, S128);
-            ok &= make_map(enc, mp + o + kMapB, lo ? M.bl : M.bh, M.sp, M.sp, sp2, kBM, kBK, false, S128);
+            ok &= make_map(enc, mp + o + kMapXK0, x[0], M.sp, M.Lp, xp, kBM, bk, false, SK);
+            ok &= make_map(enc, mp + o + kMapXK1, x[1], M.sp, M.Lp, xp, kBM, bk, false, SK);
+            ok &= make_map(enc, mp + o + kMapXM0, x[0], M.sp, M.Lp, xp, bk, 64, false, S128);
+            ok &= make_map(enc, mp + o + kMapXM1, x[1], M.sp, M.Lp, xp, bk, 64, false, S128);
+            ok &= make_map(enc, mp + o + kMapA, lo ? M.al : M.ah, M.sp, M.sp, sp2, kBM, bk, false, SK);
+            ok &= make_map(enc, mp + o + kMapB, lo ? M.bl : M.bh, M.sp, M.sp, sp2, kBM, bk, false, SK);
         }
         if (P->nsplit == 1) {
             ok &= make_map(enc, mp + kMapEXF, M.xf, M.sp, M.Lp, (int64_t)M.Lp * 4, 32, 32, true, S128);
@@ -1029,55 +1088,61 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
         need[2 * i + 1] = (int)(ph[kSquare].size() - s0);
     }
     cudaError_t e = cudaMemcpy(d_mats, mats, sizeof(DevMat) * count, cudaMemcpyHostToDevice);
-    for (int k = 0; k < 3; ++k) sort_phase(ph[k]);
-    std::vector<HostTile> fused;
-    for (int k = 0; k < 3; ++k) fused.insert(fused.end(), ph[k].begin(), ph[k].end());
-    P->ntiles = (int)fused.size();
-    P->grid = std::max(1, std::min(sms, P->ntiles));
-    std::vector<int> off;
-    std::vector<TileTask> list;
-    lpt_assign(fused, P->grid, &off, &list);
-
+    if (e != cudaSuccess) {
+        *err = std::string("uploading descriptors: ") + cudaGetErrorString(e);
+        return PE_ECUDA;
+    }
+    P->sms = sms;
+    P->mat_cost.assign(count, 0.0);
+    for (int k = 0; k < 3; ++k) {
+        P->ph_t[k].clear();
+        P->ph_c[k].clear();
+        for (const HostTile& h : ph[k]) {
+            P->ph_t[k].push_back(h.t);
+            P->ph_c[k].push_back(h.cost);
+            P->mat_cost[h.t.mat] += h.cost;
+        }
+    }
+    const size_t ntot = ph[0].size() + ph[1].size() + ph[2].size();
     size_t o = 0;
     char* base = ws;
     auto take = [&](size_t bytes, size_t al) { o = align_up(o, al); char* p = base + o; o += bytes; return p; };
     P->maps = take(sizeof(CUtensorMap) * maps.size(), 1024);
-    P->tiles = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (list.size() + 1), 256));
-    P->tile_off = reinterpret_cast<int*>(take(sizeof(int) * (off.size()), 256));
+    P->tiles = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (ntot + 1), 256));
+    P->tile_off = reinterpret_cast<int*>(take(sizeof(int) * (sms + 1), 256));
     P->need = reinterpret_cast<int*>(take(sizeof(int) * 2 * count, 256));
-    if (e == cudaSuccess)
-        e = cudaMemcpy(P->maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(P->tiles, list.data(), sizeof(TileTask) * list.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(P->tile_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(P->need, need.data(), sizeof(int) * need.size(), cudaMemcpyHostToDevice);
-    // phased schedules: one list per phase, concatenated after the fused one
-    TileTask* ph_base = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (list.size() + 1), 256));
+    TileTask* ph_base = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (ntot + 1), 256));
     size_t ph_pos = 0;
-    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
-        std::vector<int> poff;
-        std::vector<TileTask> plist;
-        const int g = std::max(1, std::min(sms, (int)ph[k].size()));
-        lpt_assign(ph[k], g, &poff, &plist);
-        P->grid_phase[k] = ph[k].empty() ? 0 : g;
+    for (int k = 0; k < 3; ++k) {
         P->ph_tiles[k] = ph_base + ph_pos;
-        P->ph_off[k] = reinterpret_cast<int*>(take(sizeof(int) * poff.size(), 256));
-        if (!plist.empty())
-            e = cudaMemcpy(P->ph_tiles[k], plist.data(), sizeof(TileTask) * plist.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(P->ph_off[k], poff.data(), sizeof(int) * poff.size(), cudaMemcpyHostToDevice);
-        ph_pos += plist.size();
-    }
-    if (e != cudaSuccess) {
-        *err = std::string("uploading the tile schedule: ") + cudaGetErrorString(e);
-        return PE_ECUDA;
+        P->ph_off[k] = reinterpret_cast<int*>(take(sizeof(int) * (sms + 1), 256));
+        ph_pos += ph[k].size();
     }
     if (o > ws_bytes) {
         *err = "internal: tcgen05 workspace too small";
         return PE_ECUDA;
     }
-    P->smem_bytes = (P->nsplit == 3) ? Cfg<3>::kSmem : Cfg<1>::kSmem;
-    e = cudaFuncSetAttribute(umma_step_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<1>::kSmem);
+    e = cudaMemcpy(P->maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->need, need.data(), sizeof(int) * need.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        *err = std::string("uploading tensor maps: ") + cudaGetErrorString(e);
+        return PE_ECUDA;
+    }
+    int st = umma_schedule(P, P->order, err);
+    if (st != PE_OK) return st;
+    if (P->nsplit == 3) P->smem_bytes = (P->bk == 64) ? Cfg<3, 64>::kSmem : Cfg<3, 32>::kSmem;
+    else P->smem_bytes = (P->bk == 64) ? Cfg<1, 64>::kSmem : Cfg<1, 32>::kSmem;
+    e = cudaFuncSetAttribute(umma_step_kernel<1, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Cfg<1, 64>::kSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(umma_step_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<3>::kSmem);
+        e = cudaFuncSetAttribute(umma_step_kernel<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Cfg<1, 32>::kSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(umma_step_kernel<3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Cfg<3, 64>::kSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(umma_step_kernel<3, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Cfg<3, 32>::kSmem);
     if (e != cudaSuccess) {
         *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
         return PE_ECUDA;
@@ -1117,8 +1182,12 @@ cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, i
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         ++*launched;
-        if (P->nsplit == 3) return cudaLaunchKernelEx(&cfg, umma_step_kernel<3>, A);
-        return cudaLaunchKernelEx(&cfg, umma_step_kernel<1>, A);
+        if (P->nsplit == 3) {
+            if (P->bk == 64) return cudaLaunchKernelEx(&cfg, umma_step_kernel<3, 64>, A);
+            return cudaLaunchKernelEx(&cfg, umma_step_kernel<3, 32>, A);
+        }
+        if (P->bk == 64) return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64>, A);
+        return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 32>, A);
     };
     if (phase < 0) {
         A.off = P->tile_off;

@@ -29,8 +29,15 @@ struct UmmaPlan {
     const DevMat* d_mats = nullptr;
     size_t smem_bytes = 0;
     int apply_bn = 256;
+    int bk = 64;             // k-block of the tcgen05 kernel (64 or 32)
+    int order = 0;           // tile order inside a phase (see sort_phase)
     void* prof = nullptr;    // optional device buffer of 16 int64 per CTA (debug)
     const float* nscale = nullptr;   // device: per-matrix normalisation factors
+    // host copy of the per-phase tiles and their costs (for re-scheduling)
+    int sms = 0;
+    std::vector<TileTask> ph_t[3];
+    std::vector<double> ph_c[3];
+    std::vector<double> mat_cost;
 };
 
 size_t umma_workspace_bytes(const DevMat* mats, int count);
@@ -40,6 +47,10 @@ size_t umma_workspace_bytes(const DevMat* mats, int count);
 // descriptors to d_mats.
 int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, int sms,
                char* ws, size_t ws_bytes, int* counters, bool tune, std::string* err);
+
+// Rebuilds and uploads the fused and phased tile schedules for a tile order
+// (0 longest-first, 1 column-grouped raster).
+int umma_schedule(UmmaPlan* P, int order, std::string* err);
 
 // Enqueue polynomial step t (0-based). phase < 0: one persistent launch of
 // the whole step with per-matrix readiness waits; phase 0/1/2: one grouped

@@ -254,3 +254,28 @@ def test_empty_and_bad_shapes_rejected():
     with pytest.raises(pe.PolarExpressError):
         pe.pe_polar(X, table(1e-3, 2), "bf16")
     assert pe.pe_polar_batched([], table(1e-3, 2), "bf16") == []
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "bf16x3"])
+def test_kblock_and_order_variants_bitwise(dtype):
+    """The 32-wide k-block variant and the column-grouped tile order issue the
+    same K=16 MMA chain per tile, so every variant gives identical bits."""
+    mats = _uneven(seed=21)
+    tab = table(1e-3, 4)
+    outs = []
+    try:
+        for bk, order in ((64, 0), (32, 0), (64, 1), (32, 1)):
+            pe.pe_debug_set(5, bk)
+            pe.pe_debug_set(6, order)
+            pe.pe_release()
+            Xs = [to_dev(G) for G in mats]
+            pe.pe_polar_batched(Xs, tab, dtype)
+            pe.pe_sync_status()
+            outs.append([X.cpu() for X in Xs])
+    finally:
+        pe.pe_debug_set(5, 0)
+        pe.pe_debug_set(6, -1)
+        pe.pe_release()
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert torch.equal(a, b)
