@@ -188,8 +188,9 @@ int pe_polar_batched_ex(void* const* X, const int64_t* m, const int64_t* n, int 
 
 /*
  * pe_sync_status -- synchronise `stream` and report (then clear) the device
- * status word of the current device: PE_OK, PE_ETIMEOUT (a bounded wait
- * expired), PE_ECUDA (a kernel error or a non-finite norm).
+ * status word of the current device: PE_OK, PE_ETIMEOUT (a bounded readiness
+ * or pipeline wait expired), PE_ECUDA (a kernel error, a non-finite norm, or
+ * mismatched tensor-memory bases in a 2-SM pair).
  */
 int pe_sync_status(void* stream);
 
@@ -232,8 +233,15 @@ void pe_release(void);
  *          tcgen05 launches fill with per-role cycle counters (0 disables;
  *          while set, calls enqueue directly, without a graph).
  *   key 5: k-block (32 or 64) of tcgen05 plans built from now on (0 = default).
- *   key 6: tile order (0 longest-first, 1 column-grouped raster) of tcgen05
- *          plans built from now on (-1 = default).
+ *   key 6: tile order of tcgen05 plans built from now on (-1 = autotuned):
+ *          0 phase-major longest-first, 1 phase-major column-grouped raster,
+ *          2/3/4 lagged interleave of phases across matrices (lag 4/8/16).
+ *   key 7: kernel mode of tcgen05 plans built from now on (-1 = autotuned,
+ *          0 = one CTA per 128x256 tile, 1 = CTA pairs sharing B by TMA
+ *          multicast, 2 = 2-SM UMMA on 256x256 tiles when every size is a
+ *          multiple of 256).
+ *   key 8: accumulators per CTA of 2-SM plans built from now on (1 or 2;
+ *          0 = default).
  * Returns PE_EINVAL for an unknown key.
  */
 int pe_debug_set(int key, int64_t value);

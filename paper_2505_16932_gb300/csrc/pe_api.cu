@@ -35,6 +35,8 @@ bool g_dbg_fail_alloc = false;
 void* g_dbg_prof = nullptr;
 int g_dbg_bk = 0;      // 0: default k-block
 int g_dbg_order = -1;  // -1: default tile order
+int g_dbg_mode = -1;   // -1: autotuned; 0 / 1 / 2: force the tcgen05 kernel mode
+int g_dbg_nacc = 0;    // 0: default accumulators of 2-SM plans; 1 or 2
 
 // tracing: (kind, start, stop) event triples recorded on the call's stream
 struct TraceRec { int kind; cudaEvent_t a, b; };
@@ -315,6 +317,8 @@ int build_plan(const PlanKey& key, Plan** out) {
         P->umma.nscale = P->d_nscale;
         if (g_dbg_bk == 32 || g_dbg_bk == 64) P->umma.bk = g_dbg_bk;
         if (g_dbg_order >= 0) P->umma.order = g_dbg_order;
+        if (g_dbg_mode >= 0) P->umma.mode = g_dbg_mode;
+        if (g_dbg_nacc == 1 || g_dbg_nacc == 2) P->umma.nacc = g_dbg_nacc;
         int ust = umma_build(&P->umma, P->mats.data(), P->d_mats, count, dtype, P->ds->sms,
                              base + o_umma, umma_bytes, P->d_counters, tune, &g_err);
         if (ust != PE_OK) return ust;
@@ -382,7 +386,8 @@ int enqueue(Plan* P, cudaStream_t st, bool tuning = false) {
 // schedules on the plan's own workspace (enqueue with `tuning`: the caller's
 // buffer is read by prepare but never written). Results are cached per
 // device and shape signature in memory and, when PE_AUTOTUNE_CACHE names a
-// file, in that file as JSON lines {"key": "...", "order": n}.
+// file, in that file as JSON lines {"key": "...", "order": n} with
+// n = 16 * kernel mode + tile order.
 
 std::map<std::string, int> g_tune;
 bool g_tune_loaded = false;
@@ -437,17 +442,30 @@ int autotune(Plan* P, cudaStream_t st) {
     const std::string key = tune_key(P->key, P->ds);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-        if (it->second != P->umma.order) return umma_schedule(&P->umma, it->second, &g_err);
-        return PE_OK;
+        const int mode = it->second / 16, order = it->second % 16;
+        if ((mode == 1 && P->umma.max_clusters < 1) || (mode == 2 && P->umma.max_clusters2 < 1))
+            return PE_OK;   // cached on another configuration
+        P->umma.mode = mode;
+        return umma_schedule(&P->umma, order, &g_err);
     }
     cudaEvent_t a = nullptr, b = nullptr;
     PE_CU(cudaEventCreate(&a));
     PE_CU(cudaEventCreate(&b));
     PE_CU(cudaStreamSynchronize(st));
     float best = 1e30f;
-    int best_order = P->umma.order;
+    int best_order = P->umma.order, best_mode = P->umma.mode;
     int r = PE_OK;
-    for (int order = 0; order < 2 && r == PE_OK; ++order) {
+    const int n_orders = (P->key.count >= 8) ? 5 : 2;   // lagged interleaves need several matrices
+    std::vector<int> modes;
+    if (g_dbg_mode >= 0) modes.push_back(P->umma.mode);
+    else {
+        modes.push_back(0);
+        if (P->umma.max_clusters > 0) modes.push_back(1);
+        if (P->umma.max_clusters2 > 0) modes.push_back(2);
+    }
+    for (int cand = 0; cand < n_orders * (int)modes.size() && r == PE_OK; ++cand) {
+        const int order = cand % n_orders;
+        P->umma.mode = modes[cand / n_orders];
         r = umma_schedule(&P->umma, order, &g_err);
         if (r != PE_OK) break;
         float ms = 0.f;
@@ -461,14 +479,15 @@ int autotune(Plan* P, cudaStream_t st) {
         if (r == PE_OK && ms < best) {
             best = ms;
             best_order = order;
+            best_mode = P->umma.mode;
         }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (r != PE_OK) return r;
-    tune_store(key, best_order);
-    if (best_order != P->umma.order) return umma_schedule(&P->umma, best_order, &g_err);
-    return PE_OK;
+    tune_store(key, 16 * best_mode + best_order);
+    P->umma.mode = best_mode;
+    return umma_schedule(&P->umma, best_order, &g_err);
 }
 
 int get_plan(const PlanKey& key, cudaStream_t st, Plan** out, bool* fresh) {
@@ -638,6 +657,8 @@ int pe_sync_status(void* stream) {
     e = cudaMemset(d->status, 0, sizeof(int));
     if (e != cudaSuccess) return pe::cuda_fail(e, "clearing the status word");
     if (h & 1) return pe::fail(PE_ETIMEOUT, "a bounded device wait expired; results are invalid");
+    if (h & 4) return pe::fail(PE_ETIMEOUT, "a pipeline wait of a tcgen05 kernel expired; results are invalid");
+    if (h & 8) return pe::fail(PE_ECUDA, "the CTAs of a 2-SM pair got different TMEM bases; results are invalid");
     if (h & 2) return pe::fail(PE_ECUDA, "non-finite Frobenius norm in the input");
     return PE_OK;
 }
@@ -691,6 +712,8 @@ int pe_debug_set(int key, int64_t value) {
         case 4: pe::g_dbg_prof = reinterpret_cast<void*>(value); return PE_OK;
         case 5: pe::g_dbg_bk = (int)value; return PE_OK;
         case 6: pe::g_dbg_order = (int)value; return PE_OK;
+        case 7: pe::g_dbg_mode = (int)value; return PE_OK;
+        case 8: pe::g_dbg_nacc = (int)value; return PE_OK;
         default: return pe::fail(PE_EINVAL, "unknown debug key");
     }
 }

@@ -52,7 +52,6 @@ constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 64 + kEpiThreads;
 constexpr int kBM = 128;        // UMMA M
 constexpr int kBN = 256;        // tile width (UMMA N, <= 256)
-constexpr int kTmemCols = 512;  // two 256-column accumulators
 // The k-block BK (64 or 32 BF16 elements: one 128- or 64-byte swizzle row)
 // is a template parameter; a smaller k-block gives more, smaller pipeline
 // stages in the same shared memory.
@@ -143,6 +142,57 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// Multicast load: the box lands at the same shared-memory offset in every CTA
+// of `mask` (within the cluster) and completes bytes on each one's mbarrier at
+// the same offset.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
+// shared::cluster address of the same offset in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+// 2-SM form: the box lands in this CTA's shared memory, the bytes complete on
+// an mbarrier that may live in the peer CTA (shared::cluster address).
+__device__ __forceinline__ void tma_load_2d_cg2(uint32_t dst, const CUtensorMap* map, uint32_t bar_cluster, int x,
+                                                int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar_cluster)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_shared_cluster_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
                      reinterpret_cast<uint64_t>(map)),
@@ -185,9 +235,38 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
 
+__device__ __forceinline__ void umma_bf16_cg2(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                              uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit_cg2_mc(uint64_t* bar, uint16_t mask) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                     smem_u32(bar)),
+                 "h"(mask)
+                 : "memory");
+}
+
+__device__ __forceinline__ void umma_commit_cg2(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
+                 : "memory");
+}
+
+// commit that arrives on the barrier at the same offset in every CTA of `mask`
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                     smem_u32(bar)),
+                 "h"(mask)
                  : "memory");
 }
 
@@ -251,6 +330,12 @@ __device__ void wait_counter(const int* cnt, int target, uint64_t limit, int* st
 
 // ------------------------------------------------------------ tile geometry
 
+// TileTask::kind carries the product in its low bits; kDummyBit marks the
+// idle member of a cluster pair (it loads its half of the shared operand for
+// its partner, computes and stores nothing).
+constexpr int kKindMask = 3;
+constexpr int kDummyBit = 0x100;
+
 struct Geo {
     int kind, mat, tm, tn, bn, nkb;
     int mapA, mapB;      // hi operand maps
@@ -262,18 +347,18 @@ struct Geo {
 template <int BK>
 __device__ __forceinline__ Geo tile_geo(const TileTask& tk, const DevMat& M, int cur) {
     Geo g;
-    g.kind = tk.kind;
+    g.kind = tk.kind & kKindMask;
     g.mat = tk.mat;
     g.tm = tk.tm;
     g.tn = tk.tn;
     g.ya = tk.tm * kBM;
     g.b0 = tk.tn * kBN;
     g.col0 = g.b0;
-    if (tk.kind == kGram) {
+    if (g.kind == kGram) {
         g.bn = min(kBN, M.sp - g.b0);
         g.nkb = M.Lp / BK;
         g.mapA = g.mapB = cur ? kMapXK1 : kMapXK0;
-    } else if (tk.kind == kSquare) {
+    } else if (g.kind == kSquare) {
         g.bn = min(kBN, M.sp - g.b0);
         g.nkb = M.sp / BK;
         g.mapA = g.mapB = kMapA;
@@ -479,13 +564,16 @@ __device__ __forceinline__ void chunk_hl(const Geo& g, const DevMat& M, const St
 
 // -------------------------------------------------------------- kernel
 
-template <int NS, int BK>
+// MODE 0: one CTA per 128 x 256 tile. MODE 1: cluster pair sharing B by
+// multicast. MODE 2: 2-SM UMMA (cta_group::2) on 256 x 256 tiles, each CTA
+// holding half of A (its 128 rows) and half of B (128 of the 256 columns).
+template <int NS, int BK, int MODE = 0>
 struct Cfg {
     static constexpr int kABytes = kBM * BK * 2;      // A tile of one k-block
-    static constexpr int kBBytes = kBN * BK * 2;      // B tile of one k-block
+    static constexpr int kBBytes = ((MODE == 2) ? kBN / 2 : kBN) * BK * 2;   // B tile (or half) of one k-block
     static constexpr int kAOps = (NS == 1) ? 1 : 2;   // stage: A hi | [A lo] | B hi | [B lo]
     static constexpr int kStage = kAOps * (kABytes + kBBytes);
-    static constexpr int kStages = ((NS == 1) ? 3 : 2) * (64 / BK);
+    static constexpr int kStages = (MODE == 2) ? 4 : ((NS == 1) ? 3 : 2) * (64 / BK);
     static constexpr uint32_t kSwzK = (BK == 64) ? 2u : 4u;   // K-major operand swizzle
     static constexpr uint32_t kSboK = 8 * BK * 2;             // 8 rows of one k-block
     static constexpr int kEpiOff = kStages * kStage;
@@ -500,9 +588,21 @@ enum ProfSlot {
     kPMma = 12
 };
 
-template <int NS, int BK>
+// MC = 1: clusters of two CTAs run a pair of tiles that share the B operand
+// (same matrix, product and tile column; adjacent 128-row blocks). Each CTA
+// loads its own A and half of B, multicasting the half to both CTAs, so each
+// SM pulls 32 KB per k-block instead of 48 KB; a stage is free once both
+// CTAs' MMAs have consumed it (both commit to both CTAs' empty barriers).
+// MODE = 2: clusters of two CTAs run one 256 x 256 tile with 2-SM UMMA; the
+// even CTA issues the MMAs (M = 256), each CTA loads its half of A and B and
+// reads its 128 accumulator rows from its own TMEM. NACC accumulators of 256
+// columns are allocated (two give epilogue / MMA overlap).
+template <int NS, int BK, int MODE, int NACC>
 __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_constant__ StepArgs A) {
-    using C = Cfg<NS, BK>;
+    using C = Cfg<NS, BK, MODE>;
+    constexpr bool MC = (MODE == 1);
+    constexpr bool kCg2 = (MODE == 2);
+    constexpr int kCols = 256 * NACC;
     constexpr int kABytes = C::kABytes;
     constexpr int kBBytes = C::kBBytes;
     constexpr int NST = C::kStages;
@@ -519,18 +619,23 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t limit = A.wait_ns ? A.wait_ns : kDefaultWaitNs;
-    const int t_begin = A.off[blockIdx.x], t_end = A.off[blockIdx.x + 1];
+    const int crank = (MODE != 0) ? (int)cluster_rank() : 0;
+    const int unit = (MODE != 0) ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    const int t_begin = A.off[unit];
+    int t_end = A.off[unit + 1];
+    // tile `it` of this CTA: pairs are stored member 0, member 1
+#define PE_TILE(it) (A.tiles[MC ? 2 * (it) + crank : (it)])   // 2-SM: both CTAs read one entry
     long long* prof = A.prof ? A.prof + 16 * blockIdx.x : nullptr;
     const long long k_t0 = clock64();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], MC ? 2 : 1);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&tfull[s], 1);
-            mbar_init(&tempty[s], kEpiThreads);
+            mbar_init(&tempty[s], kCg2 ? 2 * kEpiWarps : kEpiThreads);
         }
         mbar_init(drain, 1);
         for (int w = 0; w < kEpiWarps; ++w) mbar_init(&pfbar[w], 1);
@@ -539,14 +644,32 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
         fence_async_smem();
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(kTmemCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        if (kCg2) {
+            // one warp of each CTA of the pair performs the allocation collectively
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(tmem_slot)),
+                         "r"(kCols));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(tmem_slot)),
+                         "r"(kCols));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        }
     }
     tc_fence_before();
     __syncthreads();
+    if (MODE != 0) cluster_sync_all();   // both CTAs' barriers and TMEM exist before any cross-CTA traffic
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    if (kCg2) {
+        // the MMA addresses both CTAs' TMEM at the even CTA's base: check they match
+        const uint32_t peer = ld_shared_cluster_u32(mapa_rank(smem_u32(tmem_slot), (uint32_t)(crank ^ 1)));
+        if (peer != tmem_base) {
+            if (threadIdx.x == 0) atomicOr(A.status, 8);
+            t_end = t_begin;   // do no work; both CTAs see the mismatch
+        }
+    }
 
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------------ producer
@@ -557,7 +680,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
         bool ok = true;
         long long c_dep = 0, c_empty = 0;
         for (int it = t_begin; it < t_end && ok; ++it) {
-            const TileTask tk = A.tiles[it];
+            const TileTask tk = PE_TILE(it);
             const DevMat& M = A.mats[tk.mat];
             const Geo g = tile_geo<BK>(tk, M, A.cur);
             const CUtensorMap* mp = A.maps + (size_t)tk.mat * kMapsPerMat;
@@ -570,14 +693,33 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                 c_dep += clock64() - c0;
             }
             const uint32_t bbytes = (uint32_t)g.bn * BK * 2;
-            const uint32_t tx = (uint32_t)C::kAOps * (kABytes + bbytes);
+            // 2-SM: the even CTA's barrier receives both CTAs' halves of A and B
+            const uint32_t tx = kCg2 ? (uint32_t)(2 * (kABytes + kBBytes)) : (uint32_t)C::kAOps * (kABytes + bbytes);
+            const int ya2 = tk.tm * 2 * kBM + crank * kBM;     // 2-SM: this CTA's A rows
+            const int bh2 = g.b0 + crank * (kBN / 2);          // 2-SM: this CTA's half of B
             for (int kb = 0; kb < g.nkb; ++kb) {
                 const long long c0 = clock64();
                 if (!mbar_wait(&empty[stage], phase ^ 1, limit, abort_flag)) { ok = false; break; }
                 c_empty += clock64() - c0;
-                mbar_expect_tx(&full[stage], tx);
                 const uint32_t sbase = smem_u32(smem + stage * C::kStage);
                 const int kx = kb * BK;
+                if (kCg2) {
+                    if (crank == 0) mbar_expect_tx(&full[stage], tx);
+                    const uint32_t fb = mapa_rank(smem_u32(&full[stage]), 0);
+                    const uint32_t b_dst = sbase + kABytes;
+                    tma_load_2d_cg2(sbase, mp + g.mapA, fb, kx, ya2);
+                    if (g.kind == kApply) {
+                        tma_load_2d_cg2(b_dst, mp + g.mapB, fb, bh2, kx);
+                        tma_load_2d_cg2(b_dst + 64 * BK * 2, mp + g.mapB, fb, bh2 + 64, kx);
+                    } else {
+                        tma_load_2d_cg2(b_dst, mp + g.mapB, fb, kx, bh2);
+                    }
+                    issued |= 1u << stage;
+                    last_par = (last_par & ~(1u << stage)) | (phase << stage);
+                    if (++stage == NST) { stage = 0; phase ^= 1; }
+                    continue;
+                }
+                mbar_expect_tx(&full[stage], tx);
 #pragma unroll
                 for (int o = 0; o < C::kAOps; ++o) {
                     const int lo_off = o ? kLo : 0;
@@ -585,13 +727,27 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                     const uint32_t b_dst = sbase + C::kAOps * kABytes + o * kBBytes;
                     tma_load_2d(a_dst, mp + g.mapA + lo_off, &full[stage], kx, g.ya);
                     if (g.kind == kApply) {
-                        for (int j = 0; j < g.bn / 64; ++j)
-                            tma_load_2d(b_dst + j * (64 * BK * 2), mp + g.mapB + lo_off, &full[stage],
-                                        g.b0 + j * 64, kx);
+                        for (int j = 0; j < g.bn / 64; ++j) {
+                            if (MC) {
+                                if ((j & 1) == crank)
+                                    tma_load_2d_mc(b_dst + j * (64 * BK * 2), mp + g.mapB + lo_off, &full[stage],
+                                                   g.b0 + j * 64, kx, (uint16_t)3);
+                            } else {
+                                tma_load_2d(b_dst + j * (64 * BK * 2), mp + g.mapB + lo_off, &full[stage],
+                                            g.b0 + j * 64, kx);
+                            }
+                        }
                     } else {
-                        for (int h = 0; h < g.bn / kBM; ++h)
-                            tma_load_2d(b_dst + h * kABytes, mp + g.mapB + lo_off, &full[stage], kx,
-                                        g.b0 + h * kBM);
+                        for (int h = 0; h < g.bn / kBM; ++h) {
+                            if (MC) {
+                                if ((h & 1) == crank)
+                                    tma_load_2d_mc(b_dst + h * kABytes, mp + g.mapB + lo_off, &full[stage], kx,
+                                                   g.b0 + h * kBM, (uint16_t)3);
+                            } else {
+                                tma_load_2d(b_dst + h * kABytes, mp + g.mapB + lo_off, &full[stage], kx,
+                                            g.b0 + h * kBM);
+                            }
+                        }
                     }
                 }
                 issued |= 1u << stage;
@@ -602,9 +758,11 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
         if (!ok) {
             *abort_flag = 1;
             atomicOr(A.status, 4);
-            // let every issued copy land before the CTA can exit
-            for (int s = 0; s < NST; ++s)
-                if (issued & (1u << s)) mbar_wait(&full[s], (last_par >> s) & 1u, limit, nullptr);
+            // let every issued copy land before the CTA can exit (2-SM: the
+            // copies complete on the even CTA's barriers)
+            if (!kCg2 || crank == 0)
+                for (int s = 0; s < NST; ++s)
+                    if (issued & (1u << s)) mbar_wait(&full[s], (last_par >> s) & 1u, limit, nullptr);
         }
         if (prof) {
             prof[kPDepWait] = c_dep;
@@ -612,7 +770,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             prof[kPProducer] = clock64() - k_t0;
             prof[kPTiles] = t_end - t_begin;
         }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp == 1 && lane == 0 && (!kCg2 || crank == 0)) {
         // ------------------------------------------------------ MMA issuer
         int stage = 0;
         uint32_t phase = 0;
@@ -621,7 +779,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
         bool ok = true;
         long long c_full = 0, c_tempty = 0;
         for (int it = t_begin; it < t_end && ok; ++it) {
-            const TileTask tk = A.tiles[it];
+            const TileTask tk = PE_TILE(it);
             const DevMat& M = A.mats[tk.mat];
             const Geo g = tile_geo<BK>(tk, M, A.cur);
             long long c0 = clock64();
@@ -630,7 +788,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             tc_fence_after();
             const uint32_t d_tmem = tmem_base + acc * 256;
             const bool mn = (g.kind == kApply);
-            const uint32_t idesc = idesc_bf16(kBM, g.bn, mn);
+            const uint32_t idesc = kCg2 ? idesc_bf16(2 * kBM, kBN, mn) : idesc_bf16(kBM, g.bn, mn);
             for (int kb = 0; kb < g.nkb; ++kb) {
                 c0 = clock64();
                 if (!mbar_wait(&full[stage], phase, limit, abort_flag)) { ok = false; break; }
@@ -650,21 +808,25 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                         uint64_t bdesc;
                         if (mn) bdesc = sdesc(b_base + kk * 16 * 128, 64 * BK * 2, 1024, 2u);
                         else bdesc = sdesc(b_base + kk * 32, 16, C::kSboK, C::kSwzK);
-                        umma_bf16(d_tmem, adesc, bdesc, idesc, (kb | kk | p) != 0);
+                        if (kCg2) umma_bf16_cg2(d_tmem, adesc, bdesc, idesc, (kb | kk | p) != 0);
+                        else umma_bf16(d_tmem, adesc, bdesc, idesc, (kb | kk | p) != 0);
                     }
                 }
-                umma_commit(&empty[stage]);
+                if (kCg2) umma_commit_cg2_mc(&empty[stage], (uint16_t)3);
+                else if (MC) umma_commit_mc(&empty[stage], (uint16_t)3);
+                else umma_commit(&empty[stage]);
                 if (++stage == NST) { stage = 0; phase ^= 1; }
             }
             if (!ok) break;
-            umma_commit(&tfull[acc]);
-            acc ^= 1;
-            if (acc == 0) acc_phase ^= 1;
+            if (kCg2) umma_commit_cg2_mc(&tfull[acc], (uint16_t)3);
+            else umma_commit(&tfull[acc]);
+            if (++acc == NACC) { acc = 0; acc_phase ^= 1; }
         }
         if (!ok) {
             *abort_flag = 1;
             atomicOr(A.status, 4);
-            umma_commit(drain);
+            if (kCg2) umma_commit_cg2(drain);
+            else umma_commit(drain);
             mbar_wait(drain, 0, limit, nullptr);
         }
         if (prof) {
@@ -687,11 +849,25 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
         uint32_t acc_phase = 0;
         long long c_tfull = 0, c_dep = 0, c_gram = 0, c_sq = 0, c_ap = 0;
         for (int it = t_begin; it < t_end; ++it) {
-            const TileTask tk = A.tiles[it];
+            const TileTask tk = PE_TILE(it);
             const DevMat& M = A.mats[tk.mat];
             const Geo g = tile_geo<BK>(tk, M, A.cur);
             const CUtensorMap* mp = A.maps + (size_t)tk.mat * kMapsPerMat;
-            const int gi0 = g.tm * kBM + q * 32;    // the warp's first row
+            if (MC && (tk.kind & kDummyBit)) {
+                // idle pair member: keep the accumulator hand-off, store nothing
+                if (!mbar_wait(&tfull[acc], acc_phase, limit, abort_flag)) {
+                    *abort_flag = 1;
+                    atomicOr(A.status, 4);
+                    break;
+                }
+                tc_fence_after();
+                tc_fence_before();
+                mbar_arrive(&tempty[acc]);
+                if (++acc == NACC) { acc = 0; acc_phase ^= 1; }
+                continue;
+            }
+            // the warp's first row (2-SM: this CTA holds rows 128 crank .. of the 256-row tile)
+            const int gi0 = (kCg2 ? tk.tm * 2 * kBM + crank * kBM : g.tm * kBM) + q * 32;
             const int gi = gi0 + lane;
             const int nch = g.bn / 64;              // 32-column chunks per warpgroup
             const int cb = g.col0 + grp * nch * 32; // the warpgroup's first column
@@ -757,6 +933,9 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                         mbar_wait(&pfbar[ew], pf_phase, limit, abort_flag);
                         pf_phase ^= 1;
                         read_f32_row(s_in, lane, pre);
+                        // the refill below is an async-proxy write of the buffer
+                        // these generic-proxy reads come from
+                        fence_async_smem();
                     }
                     // every lane has read the operand and the previous chunk's
                     // stores have read their staging: refill and restage
@@ -836,7 +1015,13 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                 }
             }
             tc_fence_before();
-            mbar_arrive(&tempty[acc]);
+            if (kCg2) {
+                // one arrival per warp on the even CTA's accumulator-empty barrier
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(mapa_rank(smem_u32(&tempty[acc]), 0));
+            } else {
+                mbar_arrive(&tempty[acc]);
+            }
             if (A.dependent && sym) {
                 if (NS == 1 && lane == 0) {
                     bulk_wait0();
@@ -851,8 +1036,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             if (g.kind == kGram) c_gram += dc;
             else if (g.kind == kSquare) c_sq += dc;
             else c_ap += dc;
-            acc ^= 1;
-            if (acc == 0) acc_phase ^= 1;
+            if (++acc == NACC) { acc = 0; acc_phase ^= 1; }
         }
         if (NS == 1 && lane == 0) bulk_wait0();
         if (prof && etid == 0) {
@@ -865,10 +1049,15 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
     }
     tc_fence_before();
     __syncthreads();
+    if (MODE != 0) cluster_sync_all();   // the peer no longer touches this CTA
+#undef PE_TILE
     if (prof && threadIdx.x == 0) prof[kPTotal] = clock64() - k_t0;
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols));
+        if (kCg2)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kCols));
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kCols));
     }
 }
 
@@ -978,28 +1167,153 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
-int umma_schedule(UmmaPlan* P, int order, std::string* err) {
-    const int sms = P->sms;
-    std::vector<HostTile> ph[3];
-    for (int k = 0; k < 3; ++k) {
-        for (size_t i = 0; i < P->ph_t[k].size(); ++i) ph[k].push_back(HostTile{P->ph_t[k][i], P->ph_c[k][i]});
-        sort_phase(ph[k], order, P->mat_cost);
+// Orders of the fused list. 0, 1: phase-major (every Gram tile, then every
+// square tile, then every update tile) with the in-phase order of
+// sort_phase mode 0 / 1. 2, 3, 4: lagged interleave: a tile of phase k of the
+// matrix of cost rank r gets the key r + D k (D = 4, 8, 16), so that update
+// tiles (memory-heavy) of early matrices run beside Gram tiles
+// (compute-heavy) of later ones. Every order lists a matrix's phases in
+// dependency order, which is what the readiness waits need for progress.
+//
+// With cluster multicast (mc), the scheduling units are pairs of tiles that
+// share the B operand (same matrix, product, tile column; row blocks 2p and
+// 2p+1); a missing member becomes an idle copy of its partner.
+namespace {
+
+struct Unit {
+    TileTask t[2];   // member 0, member 1 (t[1] unused without multicast)
+    double cost;
+};
+
+std::vector<Unit> make_units(const std::vector<TileTask>& tiles, const std::vector<double>& cost, bool mc) {
+    std::vector<Unit> u;
+    if (!mc) {
+        for (size_t i = 0; i < tiles.size(); ++i) u.push_back(Unit{{tiles[i], tiles[i]}, cost[i]});
+        return u;
     }
-    std::vector<HostTile> fused;
-    for (int k = 0; k < 3; ++k) fused.insert(fused.end(), ph[k].begin(), ph[k].end());
+    // group by (matrix, tile column, row pair)
+    std::vector<size_t> idx(tiles.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
+        const TileTask &x = tiles[a], &y = tiles[b];
+        if (x.mat != y.mat) return x.mat < y.mat;
+        if (x.tn != y.tn) return x.tn < y.tn;
+        return x.tm < y.tm;
+    });
+    for (size_t k = 0; k < idx.size();) {
+        const TileTask& a = tiles[idx[k]];
+        double c = cost[idx[k]];
+        Unit v;
+        if (k + 1 < idx.size()) {
+            const TileTask& b = tiles[idx[k + 1]];
+            if (b.mat == a.mat && b.tn == a.tn && (a.tm & 1) == 0 && b.tm == a.tm + 1) {
+                v.t[0] = a;
+                v.t[1] = b;
+                v.cost = std::max(c, cost[idx[k + 1]]);
+                u.push_back(v);
+                k += 2;
+                continue;
+            }
+        }
+        TileTask d = a;
+        d.kind |= kDummyBit;
+        if (a.tm & 1) { v.t[0] = d; v.t[1] = a; }
+        else { v.t[0] = a; v.t[1] = d; }
+        v.cost = c;
+        u.push_back(v);
+        k += 1;
+    }
+    return u;
+}
+
+void sort_units(std::vector<Unit>& v, int mode, const std::vector<double>& mat_cost) {
+    std::vector<HostTile> h;
+    for (size_t i = 0; i < v.size(); ++i) {
+        TileTask key = v[i].t[(v[i].t[0].kind & kDummyBit) ? 1 : 0];
+        key.kind = (int)i;   // carry the unit index through the sort
+        h.push_back(HostTile{key, v[i].cost});
+    }
+    sort_phase(h, mode, mat_cost);
+    std::vector<Unit> out;
+    for (const HostTile& x : h) out.push_back(v[x.t.kind]);
+    v.swap(out);
+}
+
+void lpt_units(const std::vector<Unit>& order, int groups, std::vector<int>* off, std::vector<TileTask>* out, bool mc) {
+    std::vector<std::vector<int>> per(groups);
+    typedef std::pair<double, int> Load;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
+    for (int c = 0; c < groups; ++c) pq.push(Load(0.0, c));
+    for (size_t i = 0; i < order.size(); ++i) {
+        Load l = pq.top();
+        pq.pop();
+        per[l.second].push_back((int)i);
+        l.first += order[i].cost + 2.0e5;
+        pq.push(l);
+    }
+    off->assign(groups + 1, 0);
+    out->clear();
+    int n = 0;
+    for (int c = 0; c < groups; ++c) {
+        (*off)[c] = n;
+        for (int i : per[c]) {
+            out->push_back(order[i].t[0]);
+            if (mc) out->push_back(order[i].t[1]);
+            ++n;
+        }
+    }
+    (*off)[groups] = n;
+}
+
+}  // namespace
+
+int umma_schedule(UmmaPlan* P, int order, std::string* err) {
+    const bool mc = P->mode == 1;      // pairs of tiles (two list entries per unit)
+    const bool cg2 = P->mode == 2;     // one 256 x 256 tile per unit, one entry
+    const int inphase = (order == 1) ? 1 : 0;
+    std::vector<Unit> ph[3];
+    for (int k = 0; k < 3; ++k) {
+        if (cg2) ph[k] = make_units(P->ph2_t[k], P->ph2_c[k], false);
+        else ph[k] = make_units(P->ph_t[k], P->ph_c[k], mc);
+        sort_units(ph[k], inphase, P->mat_cost);
+    }
+    std::vector<Unit> fused;
+    if (order <= 1) {
+        for (int k = 0; k < 3; ++k) fused.insert(fused.end(), ph[k].begin(), ph[k].end());
+    } else {
+        const int lag = (order == 2) ? 4 : (order == 3) ? 8 : 16;
+        const int count = (int)P->mat_cost.size();
+        std::vector<int> idx(count), rank(count);
+        for (int i = 0; i < count; ++i) idx[i] = i;
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return P->mat_cost[a] > P->mat_cost[b]; });
+        for (int r = 0; r < count; ++r) rank[idx[r]] = r;
+        struct Keyed { long key; int phase; size_t pos; };
+        std::vector<Keyed> all;
+        for (int k = 0; k < 3; ++k)
+            for (size_t i = 0; i < ph[k].size(); ++i)
+                all.push_back(Keyed{(long)rank[ph[k][i].t[0].mat] + (long)lag * k, k, i});
+        std::stable_sort(all.begin(), all.end(), [](const Keyed& a, const Keyed& b) {
+            if (a.key != b.key) return a.key < b.key;
+            if (a.phase != b.phase) return a.phase < b.phase;
+            return a.pos < b.pos;
+        });
+        for (const Keyed& k : all) fused.push_back(ph[k.phase][k.pos]);
+    }
+    const int cap = mc ? P->max_clusters : cg2 ? P->max_clusters2 : P->sms;   // scheduling groups
     P->ntiles = (int)fused.size();
-    P->grid = std::max(1, std::min(sms, P->ntiles));
+    const int groups = std::max(1, std::min(cap, P->ntiles));
+    P->grid = (mc || cg2) ? 2 * groups : groups;
     std::vector<int> off;
     std::vector<TileTask> list;
-    lpt_assign(fused, P->grid, &off, &list);
+    lpt_units(fused, groups, &off, &list, mc);
     cudaError_t e = cudaMemcpy(P->tiles, list.data(), sizeof(TileTask) * list.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->tile_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
         std::vector<int> poff;
         std::vector<TileTask> plist;
-        const int g = std::max(1, std::min(sms, (int)ph[k].size()));
-        lpt_assign(ph[k], g, &poff, &plist);
-        P->grid_phase[k] = ph[k].empty() ? 0 : g;
+        const int g = std::max(1, std::min(cap, (int)ph[k].size()));
+        lpt_units(ph[k], g, &poff, &plist, mc);
+        P->grid_phase[k] = ph[k].empty() ? 0 : ((mc || cg2) ? 2 * g : g);
         if (!plist.empty())
             e = cudaMemcpy(P->ph_tiles[k], plist.data(), sizeof(TileTask) * plist.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(P->ph_off[k], poff.data(), sizeof(int) * poff.size(), cudaMemcpyHostToDevice);
@@ -1022,9 +1336,9 @@ size_t umma_workspace_bytes(const DevMat* mats, int count) {
     }
     size_t b = 0;
     b += align_up(sizeof(CUtensorMap) * kMapsPerMat * count, 1024);
-    b += 2 * align_up(sizeof(TileTask) * (tiles + 1), 256);   // fused + phased lists
+    b += 2 * align_up(sizeof(TileTask) * (2 * tiles + 2), 256);   // fused + phased lists (pairs: 2 per unit)
     b += 4 * align_up(sizeof(int) * (4096 + 1), 256);         // CSR offsets (grid <= 4096)
-    b += align_up(sizeof(int) * 2 * count, 256);
+    b += 2 * align_up(sizeof(int) * 2 * count, 256);
     return b + 4096;
 }
 
@@ -1108,15 +1422,16 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
     char* base = ws;
     auto take = [&](size_t bytes, size_t al) { o = align_up(o, al); char* p = base + o; o += bytes; return p; };
     P->maps = take(sizeof(CUtensorMap) * maps.size(), 1024);
-    P->tiles = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (ntot + 1), 256));
+    P->tiles = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (2 * ntot + 2), 256));
     P->tile_off = reinterpret_cast<int*>(take(sizeof(int) * (sms + 1), 256));
     P->need = reinterpret_cast<int*>(take(sizeof(int) * 2 * count, 256));
-    TileTask* ph_base = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (ntot + 1), 256));
+    P->need2 = reinterpret_cast<int*>(take(sizeof(int) * 2 * count, 256));
+    TileTask* ph_base = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (2 * ntot + 2), 256));
     size_t ph_pos = 0;
     for (int k = 0; k < 3; ++k) {
         P->ph_tiles[k] = ph_base + ph_pos;
         P->ph_off[k] = reinterpret_cast<int*>(take(sizeof(int) * (sms + 1), 256));
-        ph_pos += ph[k].size();
+        ph_pos += 2 * ph[k].size();
     }
     if (o > ws_bytes) {
         *err = "internal: tcgen05 workspace too small";
@@ -1128,26 +1443,104 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
         *err = std::string("uploading tensor maps: ") + cudaGetErrorString(e);
         return PE_ECUDA;
     }
-    int st = umma_schedule(P, P->order, err);
-    if (st != PE_OK) return st;
     if (P->nsplit == 3) P->smem_bytes = (P->bk == 64) ? Cfg<3, 64>::kSmem : Cfg<3, 32>::kSmem;
     else P->smem_bytes = (P->bk == 64) ? Cfg<1, 64>::kSmem : Cfg<1, 32>::kSmem;
-    e = cudaFuncSetAttribute(umma_step_kernel<1, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    P->smem_bytes2 = Cfg<1, 64, 2>::kSmem;
+    e = cudaFuncSetAttribute(umma_step_kernel<1, 64, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Cfg<1, 64>::kSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(umma_step_kernel<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(umma_step_kernel<1, 32, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Cfg<1, 32>::kSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(umma_step_kernel<3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(umma_step_kernel<1, 64, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Cfg<1, 64>::kSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(umma_step_kernel<3, 64, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Cfg<3, 64>::kSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(umma_step_kernel<3, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(umma_step_kernel<3, 32, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Cfg<3, 32>::kSmem);
     if (e != cudaSuccess) {
         *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
         return PE_ECUDA;
     }
-    return PE_OK;
+    // clusters of two CTAs that can be resident at once (multicast variant)
+    P->max_clusters = 0;
+    if (P->nsplit == 1 && P->bk == 64) {   // multicast pairs
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = dim3(2 * (sms / 2));
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = Cfg<1, 64>::kSmem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, umma_step_kernel<1, 64, 1, 2>, &cfg) == cudaSuccess)
+            P->max_clusters = std::min(n, sms / 2);
+        cudaGetLastError();
+    }
+    // 2-SM UMMA: 256 x 256 tiles, needs every padded size to be a multiple of 256
+    P->max_clusters2 = 0;
+    bool even = (P->nsplit == 1 && P->bk == 64);
+    for (int i = 0; i < count && even; ++i) even = (mats[i].sp % 256 == 0) && (mats[i].Lp % 256 == 0);
+    if (even) {
+        std::vector<int> need2(2 * count, 0);
+        for (int k = 0; k < 3; ++k) {
+            P->ph2_t[k].clear();
+            P->ph2_c[k].clear();
+        }
+        for (int i = 0; i < count; ++i) {
+            const DevMat& M = mats[i];
+            const int t2 = M.sp / 256, tl = M.Lp / 256;
+            for (int a = 0; a < t2; ++a)
+                for (int b = a; b < t2; ++b) {
+                    P->ph2_t[kGram].push_back(TileTask{i, a, b, kGram});
+                    P->ph2_c[kGram].push_back(256.0 * 256.0 * M.Lp);
+                    P->ph2_t[kSquare].push_back(TileTask{i, a, b, kSquare});
+                    P->ph2_c[kSquare].push_back(256.0 * 256.0 * M.sp);
+                    need2[2 * i] += 2;       // each CTA of the pair signals its half
+                    need2[2 * i + 1] += 2;
+                }
+            for (int a = 0; a < t2; ++a)
+                for (int b = 0; b < tl; ++b) {
+                    P->ph2_t[kApply].push_back(TileTask{i, a, b, kApply});
+                    P->ph2_c[kApply].push_back(256.0 * 256.0 * M.sp);
+                }
+        }
+        e = cudaFuncSetAttribute(umma_step_kernel<1, 64, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Cfg<1, 64, 2>::kSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(umma_step_kernel<1, 64, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)Cfg<1, 64, 2>::kSmem);
+        if (e == cudaSuccess && P->need2)
+            e = cudaMemcpy(P->need2, need2.data(), sizeof(int) * need2.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && P->need2) {
+            cudaLaunchConfig_t cfg;
+            memset(&cfg, 0, sizeof(cfg));
+            cfg.gridDim = dim3(2 * (sms / 2));
+            cfg.blockDim = dim3(kThreads);
+            cfg.dynamicSmemBytes = Cfg<1, 64, 2>::kSmem;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 2;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, umma_step_kernel<1, 64, 2, 2>, &cfg) == cudaSuccess)
+                P->max_clusters2 = std::min(n, sms / 2);
+        }
+        cudaGetLastError();
+    }
+    if (P->mode == 1 && P->max_clusters < 1) P->mode = 0;
+    if (P->mode == 2 && P->max_clusters2 < 1) P->mode = 0;
+    return umma_schedule(P, P->order, err);
 }
 
 cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, int phase, int withhold,
@@ -1156,7 +1549,7 @@ cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, i
     A.nscale = P->nscale;
     A.mats = P->d_mats;
     A.maps = reinterpret_cast<const CUtensorMap*>(P->maps);
-    A.need = P->need;
+    A.need = (P->mode == 2) ? P->need2 : P->need;
     A.counters = P->counters;
     A.status = status;
     A.a = a;
@@ -1174,20 +1567,34 @@ cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, i
         memset(&cfg, 0, sizeof(cfg));
         cfg.gridDim = dim3(grid);
         cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = P->smem_bytes;
+        cfg.dynamicSmemBytes = (P->mode == 2) ? P->smem_bytes2 : P->smem_bytes;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeCooperative;
-        attr[0].val.cooperative = coop ? 1 : 0;
+        if (P->mode != 0) {
+            // clusters of two; co-residency of the whole grid comes from sizing
+            // it by cudaOccupancyMaxActiveClusters at plan time
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 2;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+        } else {
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = coop ? 1 : 0;
+        }
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         ++*launched;
         if (P->nsplit == 3) {
-            if (P->bk == 64) return cudaLaunchKernelEx(&cfg, umma_step_kernel<3, 64>, A);
-            return cudaLaunchKernelEx(&cfg, umma_step_kernel<3, 32>, A);
+            if (P->bk == 64) return cudaLaunchKernelEx(&cfg, umma_step_kernel<3, 64, 0, 2>, A);
+            return cudaLaunchKernelEx(&cfg, umma_step_kernel<3, 32, 0, 2>, A);
         }
-        if (P->bk == 64) return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64>, A);
-        return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 32>, A);
+        if (P->mode == 2) {
+            if (P->nacc == 2) return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64, 2, 2>, A);
+            return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64, 2, 1>, A);
+        }
+        if (P->mode == 1) return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64, 1, 2>, A);
+        if (P->bk == 64) return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64, 0, 2>, A);
+        return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 32, 0, 2>, A);
     };
     if (phase < 0) {
         A.off = P->tile_off;

@@ -30,7 +30,16 @@ struct UmmaPlan {
     size_t smem_bytes = 0;
     int apply_bn = 256;
     int bk = 64;             // k-block of the tcgen05 kernel (64 or 32)
-    int order = 0;           // tile order inside a phase (see sort_phase)
+    int order = 0;           // tile order (see umma_schedule)
+    int mode = 0;            // 0 one CTA per 128x256 tile; 1 cluster pairs sharing B by TMA
+                             // multicast; 2 2-SM UMMA (cta_group::2) on 256x256 tiles
+    int nacc = 2;            // accumulators per CTA in mode 2 (1 or 2)
+    int max_clusters = 0;    // co-resident clusters of two, multicast kernel (0: unavailable)
+    int max_clusters2 = 0;   // co-resident clusters of two, 2-SM kernel (0: unavailable)
+    size_t smem_bytes2 = 0;  // dynamic shared memory of the 2-SM kernel
+    int* need2 = nullptr;    // device: per matrix readiness targets of 2-SM plans
+    std::vector<TileTask> ph2_t[3];   // 256 x 256 tiles (2-SM plans)
+    std::vector<double> ph2_c[3];
     void* prof = nullptr;    // optional device buffer of 16 int64 per CTA (debug)
     const float* nscale = nullptr;   // device: per-matrix normalisation factors
     // host copy of the per-phase tiles and their costs (for re-scheduling)

@@ -118,6 +118,22 @@ def test_uneven_spike_batch_per_shape():
         assert O.rel_fro(got, ref) <= 2e-2, (wl.shapes[i], O.rel_fro(got, ref))
 
 
+@pytest.mark.parametrize("flags", [0, pe.PE_BATCH_PHASED])
+def test_uneven_batch_bitwise_deterministic(flags):
+    """Two runs of the 112-matrix batch give identical bits (catches races in
+    the epilogue's shared-memory staging, which a small batch rarely hits)."""
+    wl = synth.uneven_d1024()
+    tab = pe.pe_coeffs(5, wl.l, wl.T, 1.01)
+    outs = []
+    for _ in range(2):
+        pe.pe_release()
+        Xs = [dev(G) for G in wl.matrices]
+        pe.pe_polar_batched(Xs, tab, "bf16", flags=flags)
+        pe.pe_sync_status()
+        outs.append([X.cpu() for X in Xs])
+    assert all(torch.equal(a, b) for a, b in zip(*outs))
+
+
 def test_ill_conditioned_bf16x3_beats_bf16():
     wl = synth.ill_conditioned()
     tab = pe.pe_coeffs(5, wl.l, wl.T, 1.01)

@@ -158,6 +158,36 @@ def test_bf16_io_bf16():
 
 # ------------------------------------------- grouped, graph, determinism
 
+def _even(seed=31):
+    rng = np.random.default_rng(seed)
+    return [rng.standard_normal(s) for s in ((256, 512), (512, 256), (768, 2304), (3072, 768), (512, 512))]
+
+
+@pytest.mark.parametrize("dtype", ["bf16"])
+def test_two_sm_mode_bitwise(dtype):
+    """2-SM UMMA (256 x 256 tiles) against the 1-SM kernel on sizes that are
+    multiples of 256, with one and with two accumulators."""
+    mats = _even()
+    tab = table(1e-3, 5)
+    outs = []
+    try:
+        for mode, nacc in ((0, 0), (2, 1), (2, 2)):
+            pe.pe_debug_set(7, mode)
+            pe.pe_debug_set(8, nacc)
+            pe.pe_release()
+            Xs = [to_dev(G) for G in mats]
+            pe.pe_polar_batched(Xs, tab, dtype)
+            pe.pe_sync_status()
+            outs.append([X.cpu() for X in Xs])
+    finally:
+        pe.pe_debug_set(7, -1)
+        pe.pe_debug_set(8, 0)
+        pe.pe_release()
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert torch.equal(a, b)
+
+
 def _uneven(seed=3, k=7):
     rng = np.random.default_rng(seed)
     shapes = [(int(rng.integers(1, 700)), int(rng.integers(1, 700))) for _ in range(k)] + [(128, 1024), (1024, 128)]
@@ -258,15 +288,22 @@ def test_empty_and_bad_shapes_rejected():
 
 @pytest.mark.parametrize("dtype", ["bf16", "bf16x3"])
 def test_kblock_and_order_variants_bitwise(dtype):
-    """The 32-wide k-block variant and the column-grouped tile order issue the
-    same K=16 MMA chain per tile, so every variant gives identical bits."""
+    """The 32-wide k-block variant, the tile orders, the cluster-multicast
+    variant and the 2-SM variant issue the same K=16 MMA chain on the same
+    operands per output element, so every variant gives identical bits (the
+    2-SM mode needs every padded size to be a multiple of 256; the shapes
+    that are not fall back to the 1-SM kernel)."""
     mats = _uneven(seed=21)
     tab = table(1e-3, 4)
     outs = []
     try:
-        for bk, order in ((64, 0), (32, 0), (64, 1), (32, 1)):
+        for bk, order, mc in ((64, 0, 0), (32, 0, 0), (64, 1, 0), (32, 1, 0), (64, 2, 0), (64, 4, 0),
+                              (64, 0, 1), (64, 1, 1), (64, 3, 1), (64, 0, 2), (64, 4, 2)):
+            if mc and dtype != "bf16":
+                continue
             pe.pe_debug_set(5, bk)
             pe.pe_debug_set(6, order)
+            pe.pe_debug_set(7, mc)
             pe.pe_release()
             Xs = [to_dev(G) for G in mats]
             pe.pe_polar_batched(Xs, tab, dtype)
@@ -275,6 +312,7 @@ def test_kblock_and_order_variants_bitwise(dtype):
     finally:
         pe.pe_debug_set(5, 0)
         pe.pe_debug_set(6, -1)
+        pe.pe_debug_set(7, -1)
         pe.pe_release()
     for o in outs[1:]:
         for a, b in zip(outs[0], o):
