@@ -232,9 +232,16 @@ def run_reference(args, wl, world, rank):
     return 0
 
 
-def kernel_source_hash():
+# source files whose contents decide each kernel's DRAM traffic
+KERNEL_SOURCES = {
+    "umma_step": ("pe_umma.cu", "pe_umma.h", "pe_internal.h"),
+    "prepare": ("pe_prep.cu", "pe_internal.h"),
+}
+
+
+def kernel_source_hash(kernel: str = "umma_step"):
     h = hashlib.sha256()
-    for f in ("pe_umma.cu", "pe_umma.h", "pe_prep.cu", "pe_internal.h"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2505_16932_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -246,7 +253,7 @@ def committed_traffic(workload: str, kernel: str):
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
-    hsh = kernel_source_hash()
+    hsh = kernel_source_hash(kernel) if kernel in KERNEL_SOURCES else None
     with open(p) as f:
         for line in f:
             parts = line.split()

@@ -229,9 +229,10 @@ void pe_release(void);
  *          invalid results and PE_ETIMEOUT is latched.
  *   key 2: wait limit of the persistent kernel in nanoseconds (0 = default).
  *   key 3: make the next workspace allocation fail (value != 0).
- *   key 4: device address of a buffer of 16 int64 per persistent CTA that
- *          tcgen05 launches fill with per-role cycle counters (0 disables;
- *          while set, calls enqueue directly, without a graph).
+ *   key 4: device address of a buffer of 32 int64 per persistent CTA to
+ *          which tcgen05 launches add per-role cycle counts (the caller
+ *          zeroes it; 0 disables; while set, calls enqueue directly,
+ *          without a graph).
  *   key 5: k-block (32 or 64) of tcgen05 plans built from now on (0 = default).
  *   key 6: tile order of tcgen05 plans built from now on (-1 = autotuned):
  *          0 phase-major longest-first, 1 phase-major column-grouped raster,

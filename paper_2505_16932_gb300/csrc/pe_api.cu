@@ -188,7 +188,7 @@ int build_plan(const PlanKey& key, Plan** out) {
     // layout of the single workspace allocation
     const size_t o_mats = cv.take(sizeof(DevMat) * count, 64);
     std::vector<TileTask> prep, tl[3];
-    struct Off { size_t xf, xf2, xh0, xh1, xl0, xl1, af, ah, al, bfp, bh, bl; };
+    struct Off { size_t xf, xf2, xh0, xh1, xl0, xl1, xq, af, ah, al, bfp, bh, bl; };
     std::vector<Off> offs(count);
     int part = 0;
     for (int i = 0; i < count; ++i) {
@@ -215,18 +215,20 @@ int build_plan(const PlanKey& key, Plan** out) {
         const size_t sL = (size_t)M.sp * M.Lp, ss = (size_t)M.sp * M.sp;
         Off& o = offs[i];
         memset(&o, 0, sizeof(o));
-        o.xf = cv.take(4 * sL);
         if (dtype == PE_FP32) {
+            o.xf = cv.take(4 * sL);
             o.xf2 = cv.take(4 * sL);
             o.af = cv.take(4 * ss);
             o.bfp = cv.take(4 * ss);
         } else {
             o.xh0 = cv.take(2 * sL);
             o.xh1 = cv.take(2 * sL);
-            o.af = cv.take(4 * ss);
             o.ah = cv.take(2 * ss);
             o.bh = cv.take(2 * ss);
+            if (dtype == PE_BF16) o.xq = cv.take(sL);
             if (dtype == PE_BF16X3) {
+                o.xf = cv.take(4 * sL);
+                o.af = cv.take(4 * ss);
                 o.xl0 = cv.take(2 * sL);
                 o.xl1 = cv.take(2 * sL);
                 o.al = cv.take(2 * ss);
@@ -278,18 +280,20 @@ int build_plan(const PlanKey& key, Plan** out) {
     for (int i = 0; i < count; ++i) {
         DevMat& M = P->mats[i];
         const Off& o = offs[i];
-        M.xf = reinterpret_cast<float*>(base + o.xf);
         if (dtype == PE_FP32) {
+            M.xf = reinterpret_cast<float*>(base + o.xf);
             M.xf2 = reinterpret_cast<float*>(base + o.xf2);
             M.af = reinterpret_cast<float*>(base + o.af);
             M.bfp = reinterpret_cast<float*>(base + o.bfp);
         } else {
             M.xh[0] = reinterpret_cast<bf16*>(base + o.xh0);
             M.xh[1] = reinterpret_cast<bf16*>(base + o.xh1);
-            M.af = reinterpret_cast<float*>(base + o.af);
             M.ah = reinterpret_cast<bf16*>(base + o.ah);
             M.bh = reinterpret_cast<bf16*>(base + o.bh);
+            if (dtype == PE_BF16) M.xq = reinterpret_cast<int8_t*>(base + o.xq);
             if (dtype == PE_BF16X3) {
+                M.xf = reinterpret_cast<float*>(base + o.xf);
+                M.af = reinterpret_cast<float*>(base + o.af);
                 M.xl[0] = reinterpret_cast<bf16*>(base + o.xl0);
                 M.xl[1] = reinterpret_cast<bf16*>(base + o.xl1);
                 M.al = reinterpret_cast<bf16*>(base + o.al);
@@ -332,9 +336,9 @@ int build_plan(const PlanKey& key, Plan** out) {
 int enqueue(Plan* P, cudaStream_t st, bool tuning = false) {
     const PlanKey& k = P->key;
     int nk = 0;
-    int outputs = kPrepF32;
-    if (k.dtype != PE_FP32) outputs |= kPrepBF16;
-    if (k.dtype == PE_BF16X3) outputs |= kPrepBF16Lo;
+    int outputs = kPrepF32;                                               // FP32
+    if (k.dtype == PE_BF16) outputs = kPrepCode;                          // hi + code (compact master)
+    if (k.dtype == PE_BF16X3) outputs = kPrepF32 | kPrepBF16 | kPrepBF16Lo;
     {
         TraceScope ts(1, st);
         PE_CU(launch_prepare(P->d_mats, k.count, P->d_prep, P->n_prep, P->d_partials, k.scale, k.eps, outputs,
@@ -468,13 +472,15 @@ int autotune(Plan* P, cudaStream_t st) {
         P->umma.mode = modes[cand / n_orders];
         r = umma_schedule(&P->umma, order, &g_err);
         if (r != PE_OK) break;
-        float ms = 0.f;
-        for (int rep = 0; rep < 2 && r == PE_OK; ++rep) {   // warm-up, then timed
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3 && r == PE_OK; ++rep) {   // warm-up, then the faster of two timed runs
             cudaEventRecord(a, st);
             r = enqueue(P, st, true);
             cudaEventRecord(b, st);
             if (cudaEventSynchronize(b) != cudaSuccess) r = cuda_fail(cudaGetLastError(), "autotune");
-            cudaEventElapsedTime(&ms, a, b);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, a, b);
+            if (rep > 0 && t < ms) ms = t;
         }
         if (r == PE_OK && ms < best) {
             best = ms;

@@ -43,11 +43,13 @@ struct DevMat {
     int32_t sp, Lp;      // padded sizes (multiples of kPadS / kPadL)
     int32_t part0, npart;  // range of this matrix's prepare tiles (norm partials)
     int32_t out_tma;       // 1 when the caller's buffer admits TMA stores
-    float* xf;           // FP32 X (master; updated in place on BF16 paths)
+    float* xf;           // FP32 X (master; updated in place on the BF16x3 path)
     float* xf2;          // FP32 ping-pong partner (FP32 path)
     bf16* xh[2];         // BF16 X (hi part), ping-pong
     bf16* xl[2];         // BF16 X lo part (BF16x3), ping-pong
-    float* af;           // FP32 A = X X^T
+    int8_t* xq;          // BF16 path: code of the next 8 mantissa bits of X
+                         // below xh[cur] (see x_split), updated in place
+    float* af;           // FP32 A = X X^T (FP32, BF16x3)
     bf16* ah;            // BF16 A (hi)
     bf16* al;            // BF16 A lo (BF16x3)
     float* bfp;          // FP32 B (FP32 path)
@@ -60,7 +62,46 @@ struct TileTask { int32_t mat, tm, tn, kind; };  // kind: 0 Gram, 1 A^2, 2 updat
 enum TileKind { kGram = 0, kSquare = 1, kApply = 2 };
 
 // Which canonical buffers the prepare kernel fills.
-enum PrepOut { kPrepF32 = 1, kPrepBF16 = 2, kPrepBF16Lo = 4 };
+enum PrepOut { kPrepF32 = 1, kPrepBF16 = 2, kPrepBF16Lo = 4, kPrepCode = 8 };
+
+// Compact master of X on the BF16 path: X is kept as hi = BF16 (the MMA
+// operand) and an 8-bit code of the next 8 mantissa bits, i.e. x rounded to a
+// 16-bit mantissa, in 3 bytes instead of the 6 of an FP32 copy plus a BF16
+// operand. On the FP32 bit pattern b of x:
+//   t  = b + 0x8080,  hi = t >> 16    (BF16; rounds up from 0x7F80 of the low half)
+//   r  = b - (hi << 16) + 0x80,  code = r >> 8   (in [-128, 127]; byte 1 of r)
+//   x' = bits^-1((hi << 16) + (code << 8)),   |x' - x| <= 2^-16 |x|.
+// The rounding point 0x7F80 keeps b - (hi << 16) in [-0x8080, 0x7F80), so the
+// code never leaves a signed byte; zero maps to zero, signs never flip, and
+// everything is integer arithmetic on the bit pattern (exact, deterministic).
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// t and r of x (see above)
+__device__ __forceinline__ void x_split(float x, uint32_t& t, uint32_t& r) {
+    const uint32_t b = __float_as_uint(x);
+    t = b + 0x8080u;
+    r = b - (t & 0xFFFF0000u) + 0x80u;
+}
+
+// hi of two elements from their t, the first in the low half
+__device__ __forceinline__ uint32_t hi_pair(uint32_t t0, uint32_t t1) { return prmt(t0, t1, 0x7632u); }
+
+// codes of four elements from their r (byte 1 of each), the first in the low byte
+__device__ __forceinline__ uint32_t code_quad(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
+    return prmt(prmt(r0, r1, 0x0051u), prmt(r2, r3, 0x0051u), 0x5410u);
+}
+
+// x' from hi << 16 and byte k of a code word: prmt puts the byte in byte 1,
+// its sign in bytes 2-3 and zero in byte 0, i.e. code << 8
+__device__ __forceinline__ float x_join(uint32_t hi32, uint32_t cw, int k) {
+    const uint32_t sel = ((8u | k) << 12) | ((8u | k) << 8) | ((uint32_t)k << 4) | 4u;
+    return __uint_as_float(hi32 + prmt(cw, 0u, sel));
+}
 
 // ---- launchers (return cudaError_t of the launch) ----
 cudaError_t launch_prepare(const DevMat* mats, int nmats, const TileTask* tiles, int ntiles, double* partials,

@@ -2,8 +2,9 @@
 //   nu = ||G||_F,  X_0 = G / (scale * nu + eps),
 // in one pass over G. Each block takes one 64 x 64 tile of the canonical
 // short-side layout (X = G^T when m > n), padded with zeros to whole tiles,
-// and writes it unscaled in every precision the chosen path needs, together
-// with the tile's sum of squares. The last block to finish (atomic ticket)
+// and writes it unscaled in every precision the chosen path needs (FP32;
+// BF16 hi with the code of the next 8 bits; BF16 hi + lo), together with the tile's
+// sum of squares. The last block to finish (atomic ticket)
 // sums each matrix's tile partials in a fixed order and stores the matrix's
 // normalisation factor 1 / (scale * nu + eps); the first polynomial step
 // applies it (A = s^2 X X^T, X_1 = s (a X + B X)), which is the same map as
@@ -30,12 +31,12 @@ __device__ __forceinline__ float4 load4(const DevMat& M, bool vec, int rows, int
     const int64_t base = (int64_t)row * M.ld + col;
     if (vec && col + 3 < cols) {
         if (M.io == PE_IO_BF16) {
-            const uint2 u = *reinterpret_cast<const uint2*>(reinterpret_cast<const bf16*>(M.user) + base);
+            const uint2 u = __ldcs(reinterpret_cast<const uint2*>(reinterpret_cast<const bf16*>(M.user) + base));
             const __nv_bfloat162 p0 = *reinterpret_cast<const __nv_bfloat162*>(&u.x);
             const __nv_bfloat162 p1 = *reinterpret_cast<const __nv_bfloat162*>(&u.y);
             r = make_float4(__low2float(p0), __high2float(p0), __low2float(p1), __high2float(p1));
         } else {
-            r = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(M.user) + base);
+            r = __ldcs(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(M.user) + base));
         }
         return r;
     }
@@ -53,7 +54,16 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
 
 __device__ __forceinline__ void put4(const DevMat& M, int outputs, int64_t o, float4 v) {
     if (outputs & kPrepF32) *reinterpret_cast<float4*>(M.xf + o) = v;
-    if (outputs & (kPrepBF16 | kPrepBF16Lo)) {
+    if (outputs & kPrepCode) {
+        // BF16 path: hi and code of the compact master (x_split)
+        uint32_t t0, t1, t2, t3, r0, r1, r2, r3;
+        x_split(v.x, t0, r0);
+        x_split(v.y, t1, r1);
+        x_split(v.z, t2, r2);
+        x_split(v.w, t3, r3);
+        *reinterpret_cast<uint2*>(M.xh[0] + o) = make_uint2(hi_pair(t0, t1), hi_pair(t2, t3));
+        *reinterpret_cast<uint32_t*>(M.xq + o) = code_quad(r0, r1, r2, r3);
+    } else if (outputs & (kPrepBF16 | kPrepBF16Lo)) {
         uint2 h;
         h.x = pack2(v.x, v.y);
         h.y = pack2(v.z, v.w);
@@ -89,21 +99,28 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
     const int esz = (M.io == PE_IO_BF16) ? 2 : 4;
     const bool vec = (reinterpret_cast<uintptr_t>(M.user) % (4 * esz) == 0) && (M.ld % 4 == 0);
     float ss = 0.f;
+    // all four loads of the thread are issued before any store (the
+    // compiler cannot reorder them across stores that may alias G)
+    float4 ld[4];
     if (!M.trans) {
         // X[i][l] = G[i][l]; G is s x L
 #pragma unroll
+        for (int p = 0; p < 4; ++p) ld[p] = load4(M, vec, M.s, M.L, i0 + rr + 16 * p, l0 + c4);
+#pragma unroll
         for (int p = 0; p < 4; ++p) {
             const int r = rr + 16 * p;
-            const float4 v = load4(M, vec, M.s, M.L, i0 + r, l0 + c4);
+            const float4 v = ld[p];
             ss = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, ss))));
             put4(M, outputs, (int64_t)(i0 + r) * M.Lp + l0 + c4, v);
         }
     } else {
         // X[i][l] = G[l][i]; G is L x s: read G rows l with i contiguous, transpose in smem
 #pragma unroll
+        for (int p = 0; p < 4; ++p) ld[p] = load4(M, vec, M.L, M.s, l0 + rr + 16 * p, i0 + c4);
+#pragma unroll
         for (int p = 0; p < 4; ++p) {
             const int r = rr + 16 * p;
-            const float4 v = load4(M, vec, M.L, M.s, l0 + r, i0 + c4);
+            const float4 v = ld[p];
             ss = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, ss))));
             tile[r][c4 + 0] = v.x;
             tile[r][c4 + 1] = v.y;

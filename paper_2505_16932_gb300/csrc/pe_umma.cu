@@ -12,10 +12,13 @@
 //              columns); each warp owns 32 tile rows (its TMEM lane quarter)
 //              and works in 32 x 32 chunks.
 // BF16 epilogue: every chunk goes TMEM -> registers -> FP32 arithmetic ->
-// swizzled shared-memory staging -> TMA bulk tensor stores; the FP32 operand
-// of the epilogue (X for the update, A for the square) is fetched ahead by
-// TMA into the warp's staging buffer. Split-BF16 epilogue: the same
-// arithmetic with direct global stores.
+// swizzled shared-memory staging -> TMA bulk tensor stores; the epilogue's
+// own operand (X for the update, A for the square) is fetched ahead by TMA
+// into the warp's staging buffer. X is kept as its BF16 operand copy plus an
+// 8-bit residual code (x_code), which carries the a X term at ~2^-16
+// relative precision; b A takes the BF16 A the square reads anyway.
+// Split-BF16 epilogue: the same arithmetic on FP32 X and A with direct
+// global stores.
 //
 // The kernel is persistent and grouped: each CTA walks its own list of tiles
 // (all matrices of the call, phase-ordered Gram -> square -> update). In the
@@ -25,8 +28,9 @@
 //
 // Symmetric outputs: only 32 x 32 chunks on or above the diagonal are
 // stored. Strictly-upper chunks are stored and mirrored; a diagonal chunk is
-// symmetrised from its upper half. The FP32 copy of A keeps the upper and
-// diagonal chunks only (the square epilogue reads nothing else).
+// symmetrised from its upper half. The FP32 copy of A (split-BF16 only)
+// keeps the upper and diagonal chunks (the square epilogue reads nothing
+// else).
 //
 // Split BF16 (BF16x3): every operand is x = hi + lo with hi = bf16(x),
 // lo = bf16(x - hi); each k-step issues hi*hi + hi*lo + lo*hi into the same
@@ -63,7 +67,9 @@ enum MapIdx {
     kMapXK0 = 0, kMapXK1, kMapXM0, kMapXM1, kMapA, kMapB,
     kLo = 6,   // lo operand maps follow at +6 (BF16x3)
     // epilogue maps, 32 x 32 boxes: FP32 with 128-byte swizzle, BF16 with 64-byte
-    kMapEXF = 12, kMapEXH0, kMapEXH1, kMapEAF, kMapEAH, kMapEBH, kMapEOut,
+    // (kMapEXF, kMapEAF: reserved; kMapEXQ: codes of X, 32 x 32 bytes with
+    // 32-byte swizzle)
+    kMapEXF = 12, kMapEXH0, kMapEXH1, kMapEAF, kMapEAH, kMapEBH, kMapEOut, kMapEXQ,
     kMapsPerMat
 };
 
@@ -412,15 +418,59 @@ __device__ __forceinline__ void stage_f32_row(uint8_t* buf, int r, const float (
             make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
 }
 
-__device__ __forceinline__ void read_f32_row(const uint8_t* buf, int r, float (&v)[32]) {
+// Codes of X: 32-byte rows with 32-byte swizzle (16-byte chunk c of row r
+// lives at chunk c ^ ((r >> 2) & 1)).
+__device__ __forceinline__ uint32_t q8_off(int r, int c) {
+    return r * 32 + ((((c >> 4) ^ (r >> 2)) & 1) << 4) + (c & 15);
+}
+
+// BF16 row of a box (64-byte swizzle) as FP32
+__device__ __forceinline__ void read_bf16_row(const uint8_t* buf, int r, float (&v)[32]) {
 #pragma unroll
-    for (int c4 = 0; c4 < 8; ++c4) {
-        const float4 x = *reinterpret_cast<const float4*>(buf + f32_off(r, 4 * c4));
-        v[4 * c4] = x.x;
-        v[4 * c4 + 1] = x.y;
-        v[4 * c4 + 2] = x.z;
-        v[4 * c4 + 3] = x.w;
+    for (int c8 = 0; c8 < 4; ++c8) {
+        const uint4 u = *reinterpret_cast<const uint4*>(buf + bf16_off(r, 8 * c8));
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            v[8 * c8 + 2 * m] = __uint_as_float(w[m] << 16);   // low half: first element
+            v[8 * c8 + 2 * m + 1] = __uint_as_float(w[m] & 0xFFFF0000u);
+        }
     }
+}
+
+// X of a row from its hi box (BF16) at buf and its code box at buf + 2048
+__device__ __forceinline__ void read_x_row(const uint8_t* buf, int r, float (&v)[32]) {
+    const uint4 c0 = *reinterpret_cast<const uint4*>(buf + 2048 + q8_off(r, 0));
+    const uint4 c1 = *reinterpret_cast<const uint4*>(buf + 2048 + q8_off(r, 16));
+    const uint32_t cw[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+    for (int c8 = 0; c8 < 4; ++c8) {
+        const uint4 u = *reinterpret_cast<const uint4*>(buf + bf16_off(r, 8 * c8));
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int j = 8 * c8 + 2 * m;
+            v[j] = x_join(w[m] << 16, cw[j >> 2], j & 3);
+            v[j + 1] = x_join(w[m] & 0xFFFF0000u, cw[(j + 1) >> 2], (j + 1) & 3);
+        }
+    }
+}
+
+// a row of X as hi (BF16 box at s_h) and code (box at s_q)
+__device__ __forceinline__ void stage_x_row(uint8_t* s_h, uint8_t* s_q, int r, const float (&v)[32]) {
+    uint32_t qw[8];
+#pragma unroll
+    for (int c8 = 0; c8 < 4; ++c8) {
+        uint32_t t[8], rr[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x_split(v[8 * c8 + k], t[k], rr[k]);
+        *reinterpret_cast<uint4*>(s_h + bf16_off(r, 8 * c8)) =
+            make_uint4(hi_pair(t[0], t[1]), hi_pair(t[2], t[3]), hi_pair(t[4], t[5]), hi_pair(t[6], t[7]));
+        qw[2 * c8] = code_quad(rr[0], rr[1], rr[2], rr[3]);
+        qw[2 * c8 + 1] = code_quad(rr[4], rr[5], rr[6], rr[7]);
+    }
+    *reinterpret_cast<uint4*>(s_q + q8_off(r, 0)) = make_uint4(qw[0], qw[1], qw[2], qw[3]);
+    *reinterpret_cast<uint4*>(s_q + q8_off(r, 16)) = make_uint4(qw[4], qw[5], qw[6], qw[7]);
 }
 
 __device__ __forceinline__ void stage_bf16_row(uint8_t* buf, int r, const float (&v)[32]) {
@@ -447,14 +497,6 @@ __device__ __forceinline__ void stage_bf16_col(uint8_t* buf, int r, const float 
 }
 
 // symmetric box from the upper half held by row r: (r, c) for c >= r and (c, r) for c > r
-__device__ __forceinline__ void stage_f32_sym(uint8_t* buf, int r, const float (&v)[32]) {
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-        if (c >= r) *reinterpret_cast<float*>(buf + f32_off(r, c)) = v[c];
-        if (c > r) *reinterpret_cast<float*>(buf + f32_off(c, r)) = v[c];
-    }
-}
-
 __device__ __forceinline__ void stage_bf16_sym(uint8_t* buf, int r, const float (&v)[32]) {
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
@@ -581,11 +623,14 @@ struct Cfg {
     static constexpr size_t kSmem = 1024 + kBarOff + 512;
 };
 
-// Per-role cycle counters (debug profiling), slot k of CTA b at prof[16 b + k].
+// Per-role cycle counters (debug profiling), slot k of CTA b at prof[32 b + k].
 enum ProfSlot {
     kPTotal = 0, kPDepWait = 1, kPEmptyWait = 2, kPFullWait = 3, kPTEmptyWait = 4, kPTFullWait = 5,
     kPGramBusy = 6, kPSquareBusy = 7, kPApplyBusy = 8, kPEpiDepWait = 9, kPTiles = 10, kPProducer = 11,
-    kPMma = 12
+    kPMma = 12,
+    // update epilogue sub-steps: operand read + arithmetic, prefetch wait,
+    // output staging, wait for the output box
+    kPApRead = 13, kPApPf = 14, kPApMath = 15, kPApStore = 10, kPApFence = 16, kPApIssue = 17, kPApTmem = 18
 };
 
 // MC = 1: clusters of two CTAs run a pair of tiles that share the B operand
@@ -613,8 +658,8 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
     uint64_t* tfull = empty + NST;
     uint64_t* tempty = tfull + 2;
     uint64_t* drain = tempty + 2;
-    uint64_t* pfbar = drain + 1;            // one prefetch barrier per epilogue warp
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pfbar + kEpiWarps);
+    uint64_t* pfbar = drain + 1;            // two operand-prefetch barriers per epilogue warp
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pfbar + 2 * kEpiWarps);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -625,7 +670,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
     int t_end = A.off[unit + 1];
     // tile `it` of this CTA: pairs are stored member 0, member 1
 #define PE_TILE(it) (A.tiles[MC ? 2 * (it) + crank : (it)])   // 2-SM: both CTAs read one entry
-    long long* prof = A.prof ? A.prof + 16 * blockIdx.x : nullptr;
+    long long* prof = A.prof ? A.prof + 32 * blockIdx.x : nullptr;
     const long long k_t0 = clock64();
 
     if (threadIdx.x == 0) {
@@ -638,7 +683,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             mbar_init(&tempty[s], kCg2 ? 2 * kEpiWarps : kEpiThreads);
         }
         mbar_init(drain, 1);
-        for (int w = 0; w < kEpiWarps; ++w) mbar_init(&pfbar[w], 1);
+        for (int w = 0; w < 2 * kEpiWarps; ++w) mbar_init(&pfbar[w], 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
@@ -765,10 +810,10 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                     if (issued & (1u << s)) mbar_wait(&full[s], (last_par >> s) & 1u, limit, nullptr);
         }
         if (prof) {
-            prof[kPDepWait] = c_dep;
-            prof[kPEmptyWait] = c_empty;
-            prof[kPProducer] = clock64() - k_t0;
-            prof[kPTiles] = t_end - t_begin;
+            prof[kPDepWait] += c_dep;
+            prof[kPEmptyWait] += c_empty;
+            prof[kPProducer] += clock64() - k_t0;
+
         }
     } else if (warp == 1 && lane == 0 && (!kCg2 || crank == 0)) {
         // ------------------------------------------------------ MMA issuer
@@ -830,9 +875,9 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             mbar_wait(drain, 0, limit, nullptr);
         }
         if (prof) {
-            prof[kPFullWait] = c_full;
-            prof[kPTEmptyWait] = c_tempty;
-            prof[kPMma] = clock64() - k_t0;
+            prof[kPFullWait] += c_full;
+            prof[kPTEmptyWait] += c_tempty;
+            prof[kPMma] += clock64() - k_t0;
         }
     } else if (warp >= 2) {
         // ------------------------------------------------------ epilogue
@@ -841,13 +886,15 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
         const int grp = ew >> 2;           // column half of the tile
         const int etid = threadIdx.x - 64; // 0..255
         uint8_t* stg = smem + C::kEpiOff + ew * kWarpStage;
-        uint8_t* s_in = stg;               // FP32 operand prefetch / FP32 output (Gram)
-        uint8_t* s_out = stg + 4096;       // FP32 output (update), BF16 direct (symmetric)
-        uint8_t* s_h = stg + 8192;         // BF16 output (update); s_out + 2048: BF16 mirror
-        uint32_t pf_phase = 0;
+        // staging: two operand buffers (X hi at +0 and code at +2048, or
+        // BF16 A) of 3 KB, then the output box: X hi + code (update), FP32
+        // or BF16 result (last update), BF16 direct + mirror (symmetric)
+        uint8_t* s_out = stg + 6144;
+        uint32_t pf_issued = 0, pf_used = 0;   // operand prefetches, in order: buffer n & 1, parity (n >> 1) & 1
         int acc = 0;
         uint32_t acc_phase = 0;
-        long long c_tfull = 0, c_dep = 0, c_gram = 0, c_sq = 0, c_ap = 0;
+        long long c_tfull = 0, c_dep = 0, c_gram = 0, c_sq = 0, c_ap = 0, c_rdx = 0, c_pf = 0, c_math = 0, c_st = 0, c_fn = 0,
+                  c_is = 0, c_tm = 0;
         for (int it = t_begin; it < t_end; ++it) {
             const TileTask tk = PE_TILE(it);
             const DevMat& M = A.mats[tk.mat];
@@ -895,13 +942,26 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                 while (first < nch && chunk_class(gi0, cb + first * 32) == kChunkLower) ++first;
             }
             float pre[32];
-            const CUtensorMap* in_map = mp + ((g.kind == kApply) ? kMapEXF : kMapEAF);
-            const float* in_g = (g.kind == kApply) ? M.xf + (int64_t)gi * M.Lp : M.af + (int64_t)gi * M.sp;
+            const float* in_g = (NS == 1) ? nullptr
+                                : (g.kind == kApply) ? M.xf + (int64_t)gi * M.Lp : M.af + (int64_t)gi * M.sp;
+            // BF16 path: the epilogue operand (update: X hi + code, square:
+            // BF16 A) of each stored chunk is fetched by TMA two chunks ahead
+            const CUtensorMap* in_map = mp + ((g.kind == kApply) ? (A.cur ? kMapEXH1 : kMapEXH0) : kMapEAH);
+            const uint32_t in_bytes = (g.kind == kApply) ? 3072u : 2048u;
+            auto prefetch = [&](int ch) {
+                const int b = pf_issued & 1;
+                if (lane == 0) {
+                    const uint32_t dst = smem_u32(stg + b * 3072);
+                    mbar_expect_tx(&pfbar[2 * ew + b], in_bytes);
+                    tma_load_2d(dst, in_map, &pfbar[2 * ew + b], cb + ch * 32, gi0);
+                    if (g.kind == kApply) tma_load_2d(dst + 2048, mp + kMapEXQ, &pfbar[2 * ew + b], cb + ch * 32, gi0);
+                }
+                ++pf_issued;
+            };
             if (NS == 1) {
-                if (needs_in && first < nch && lane == 0) {
-                    bulk_wait_read0();   // s_in may still feed the previous tile's store
-                    mbar_expect_tx(&pfbar[ew], 4096);
-                    tma_load_2d(smem_u32(s_in), in_map, &pfbar[ew], cb + first * 32, gi0);
+                if (needs_in) {
+                    if (first < nch) prefetch(first);
+                    if (first + 1 < nch) prefetch(first + 1);
                 }
             } else if (needs_in && first < nch) {
                 load32(pre, in_g + cb + first * 32);
@@ -927,83 +987,82 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                 if (sym)
                     while (nx < nch && chunk_class(gi0, cb + nx * 32) == kChunkLower) ++nx;
                 float v[32];
+                const bool sub = prof && g.kind == kApply;   // debug: update epilogue sub-steps
+                long long s0c = sub ? clock64() : 0;
                 tmem_ld32(tbase + i * 32, v);
+                if (sub) { const long long t = clock64(); c_tm += t - s0c; s0c = t; }
                 if (NS == 1) {
                     if (needs_in) {
-                        mbar_wait(&pfbar[ew], pf_phase, limit, abort_flag);
-                        pf_phase ^= 1;
-                        read_f32_row(s_in, lane, pre);
-                        // the refill below is an async-proxy write of the buffer
-                        // these generic-proxy reads come from
-                        fence_async_smem();
-                    }
-                    // every lane has read the operand and the previous chunk's
-                    // stores have read their staging: refill and restage
-                    if (lane == 0) bulk_wait_read0();
-                    __syncwarp();
-                    if (needs_in && nx < nch && lane == 0) {
-                        mbar_expect_tx(&pfbar[ew], 4096);
-                        tma_load_2d(smem_u32(s_in), in_map, &pfbar[ew], cb + nx * 32, gi0);
+                        const int b = pf_used & 1;
+                        mbar_wait(&pfbar[2 * ew + b], (pf_used >> 1) & 1, limit, nullptr);
+                        if (sub) { const long long t = clock64(); c_pf += t - s0c; s0c = t; }
+                        if (g.kind == kApply) read_x_row(stg + b * 3072, lane, pre);
+                        else read_bf16_row(stg + b * 3072, lane, pre);
+                        ++pf_used;
                     }
                     if (g.kind == kApply) {
+                        if (A.step == 0) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) v[j] = s0 * fmaf(A.a, pre[j], v[j]);
-                        if (!A.last) {
-                            stage_f32_row(s_out, lane, v);
-                            stage_bf16_row(s_h, lane, v);
-                            fence_async_smem();
-                            __syncwarp();
-                            if (lane == 0) {
-                                tma_store_2d(mp + kMapEXF, smem_u32(s_out), col0, gi0);
-                                tma_store_2d(mp + (A.cur ? kMapEXH0 : kMapEXH1), smem_u32(s_h), col0, gi0);
-                                bulk_commit();
-                            }
-                        } else if (M.out_tma) {
-                            uint8_t* o = (M.io == PE_IO_BF16) ? s_h : s_out;
+                            for (int j = 0; j < 32; ++j) v[j] = s0 * fmaf(A.a, pre[j], v[j]);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) v[j] = fmaf(A.a, pre[j], v[j]);
+                        }
+                    } else if (g.kind == kSquare) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = fmaf(A.b, pre[j], A.c * v[j]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] *= s0 * s0;
+                    }
+                    if (sub) { const long long t = clock64(); c_rdx += t - s0c; s0c = t; }
+                    // the previous chunk's stores have read the output box
+                    if (lane == 0) bulk_wait_read0();
+                    __syncwarp();
+                    if (sub) { const long long t = clock64(); c_st += t - s0c; s0c = t; }
+                    const bool direct_out = !(g.kind == kApply && A.last && !M.out_tma);
+                    if (g.kind == kApply && !A.last) {
+                        stage_x_row(s_out, s_out + 2048, lane, v);
+                    } else if (g.kind == kApply) {
+                        if (M.out_tma) {
                             if (M.io == PE_IO_BF16) {
-                                if (M.trans) stage_bf16_col(o, lane, v); else stage_bf16_row(o, lane, v);
+                                if (M.trans) stage_bf16_col(s_out, lane, v); else stage_bf16_row(s_out, lane, v);
                             } else {
-                                if (M.trans) stage_f32_col(o, lane, v); else stage_f32_row(o, lane, v);
-                            }
-                            fence_async_smem();
-                            __syncwarp();
-                            if (lane == 0) {
-                                if (M.trans) tma_store_2d(mp + kMapEOut, smem_u32(o), gi0, col0);
-                                else tma_store_2d(mp + kMapEOut, smem_u32(o), col0, gi0);
-                                bulk_commit();
+                                if (M.trans) stage_f32_col(s_out, lane, v); else stage_f32_row(s_out, lane, v);
                             }
                         } else {
 #pragma unroll
                             for (int j = 0; j < 32; ++j) store_user(M, gi, col0 + j, v[j]);
                         }
+                    } else if (cls == kChunkDiag) {
+                        stage_bf16_sym(s_out, lane, v);
                     } else {
-                        if (g.kind == kSquare) {
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) v[j] = fmaf(A.b, pre[j], A.c * v[j]);
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) v[j] *= s0 * s0;
-                        }
-                        uint8_t* s_dir = s_out;
-                        uint8_t* s_mir = s_out + 2048;
-                        if (cls == kChunkDiag) {
-                            if (g.kind == kGram) stage_f32_sym(s_in, lane, v);
-                            stage_bf16_sym(s_dir, lane, v);
-                        } else {
-                            if (g.kind == kGram) stage_f32_row(s_in, lane, v);
-                            stage_bf16_row(s_dir, lane, v);
-                            stage_bf16_col(s_mir, lane, v);
-                        }
-                        fence_async_smem();
-                        __syncwarp();
-                        if (lane == 0) {
-                            const CUtensorMap* hm = mp + ((g.kind == kGram) ? kMapEAH : kMapEBH);
-                            if (g.kind == kGram) tma_store_2d(mp + kMapEAF, smem_u32(s_in), col0, gi0);
-                            tma_store_2d(hm, smem_u32(s_dir), col0, gi0);
-                            if (cls != kChunkDiag) tma_store_2d(hm, smem_u32(s_mir), gi0, col0);
-                            bulk_commit();
-                        }
+                        stage_bf16_row(s_out, lane, v);
+                        stage_bf16_col(s_out + 2048, lane, v);
                     }
+                    if (sub) { const long long t = clock64(); c_math += t - s0c; s0c = t; }
+                    // one fence orders this chunk's generic reads of the operand
+                    // buffer and writes of the output box before the async
+                    // proxy's store of the box and refill of the buffer
+                    fence_async_smem();
+                    __syncwarp();
+                    if (sub) { const long long t = clock64(); c_fn += t - s0c; s0c = t; }
+                    if (lane == 0 && direct_out) {
+                        if (g.kind == kApply && !A.last) {
+                            tma_store_2d(mp + (A.cur ? kMapEXH0 : kMapEXH1), smem_u32(s_out), col0, gi0);
+                            tma_store_2d(mp + kMapEXQ, smem_u32(s_out + 2048), col0, gi0);
+                        } else if (g.kind == kApply) {
+                            if (M.trans) tma_store_2d(mp + kMapEOut, smem_u32(s_out), gi0, col0);
+                            else tma_store_2d(mp + kMapEOut, smem_u32(s_out), col0, gi0);
+                        } else {
+                            const CUtensorMap* hm = mp + ((g.kind == kGram) ? kMapEAH : kMapEBH);
+                            tma_store_2d(hm, smem_u32(s_out), col0, gi0);
+                            if (cls != kChunkDiag) tma_store_2d(hm, smem_u32(s_out + 2048), gi0, col0);
+                        }
+                        bulk_commit();
+                    }
+                    if (needs_in && i + 2 < nch) prefetch(i + 2);
+                    if (sub) { __syncwarp(); c_is += clock64() - s0c; }
                 } else {
                     float nxt_pre[32];
                     if (needs_in && nx < nch) load32(nxt_pre, in_g + cb + nx * 32);
@@ -1038,20 +1097,29 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             else c_ap += dc;
             if (++acc == NACC) { acc = 0; acc_phase ^= 1; }
         }
+        // operand prefetches still in flight (a tile left early) land before exit
+        for (; pf_used < pf_issued; ++pf_used) mbar_wait(&pfbar[2 * ew + (pf_used & 1)], (pf_used >> 1) & 1, limit, nullptr);
         if (NS == 1 && lane == 0) bulk_wait0();
         if (prof && etid == 0) {
-            prof[kPTFullWait] = c_tfull;
-            prof[kPEpiDepWait] = c_dep;
-            prof[kPGramBusy] = c_gram;
-            prof[kPSquareBusy] = c_sq;
-            prof[kPApplyBusy] = c_ap;
+            prof[kPTFullWait] += c_tfull;
+            prof[kPEpiDepWait] += c_dep;
+            prof[kPGramBusy] += c_gram;
+            prof[kPSquareBusy] += c_sq;
+            prof[kPApplyBusy] += c_ap;
+            prof[kPApRead] += c_rdx;
+            prof[kPApPf] += c_pf;
+            prof[kPApMath] += c_math;
+            prof[kPApStore] += c_st;
+            prof[kPApFence] += c_fn;
+            prof[kPApIssue] += c_is;
+            prof[kPApTmem] += c_tm;
         }
     }
     tc_fence_before();
     __syncthreads();
     if (MODE != 0) cluster_sync_all();   // the peer no longer touches this CTA
 #undef PE_TILE
-    if (prof && threadIdx.x == 0) prof[kPTotal] = clock64() - k_t0;
+    if (prof && threadIdx.x == 0) prof[kPTotal] += clock64() - k_t0;
     if (warp == 1) {
         tc_fence_after();
         if (kCg2)
@@ -1083,12 +1151,12 @@ EncodeTiledFn encode_fn(std::string* err) {
 
 // 2-D row-major map: rows x cols, row pitch in bytes, box = box_cols x box_rows.
 bool make_map(EncodeTiledFn enc, CUtensorMap* m, const void* ptr, int64_t rows, int64_t cols, int64_t pitch,
-              int box_rows, int box_cols, bool f32, CUtensorMapSwizzle sw) {
+              int box_rows, int box_cols, CUtensorMapDataType dt, CUtensorMapSwizzle sw) {
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)pitch};
     cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = enc(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+    CUresult r = enc(m, dt, 2,
                      const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -1357,6 +1425,8 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
     std::vector<HostTile> ph[3];
     std::vector<int> need(2 * count);
     const CUtensorMapSwizzle S128 = CU_TENSOR_MAP_SWIZZLE_128B, S64 = CU_TENSOR_MAP_SWIZZLE_64B;
+    const CUtensorMapDataType BF = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                              U8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
     for (int i = 0; i < count; ++i) {
         DevMat& M = mats[i];
         CUtensorMap* mp = maps.data() + (size_t)i * kMapsPerMat;
@@ -1367,20 +1437,20 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
         for (int lo = 0; lo < (P->nsplit == 3 ? 2 : 1); ++lo) {
             bf16* const* x = lo ? M.xl : M.xh;
             const int o = lo ? kLo : 0;
-            ok &= make_map(enc, mp + o + kMapXK0, x[0], M.sp, M.Lp, xp, kBM, bk, false, SK);
-            ok &= make_map(enc, mp + o + kMapXK1, x[1], M.sp, M.Lp, xp, kBM, bk, false, SK);
-            ok &= make_map(enc, mp + o + kMapXM0, x[0], M.sp, M.Lp, xp, bk, 64, false, S128);
-            ok &= make_map(enc, mp + o + kMapXM1, x[1], M.sp, M.Lp, xp, bk, 64, false, S128);
-            ok &= make_map(enc, mp + o + kMapA, lo ? M.al : M.ah, M.sp, M.sp, sp2, kBM, bk, false, SK);
-            ok &= make_map(enc, mp + o + kMapB, lo ? M.bl : M.bh, M.sp, M.sp, sp2, kBM, bk, false, SK);
+            ok &= make_map(enc, mp + o + kMapXK0, x[0], M.sp, M.Lp, xp, kBM, bk, BF, SK);
+            ok &= make_map(enc, mp + o + kMapXK1, x[1], M.sp, M.Lp, xp, kBM, bk, BF, SK);
+            ok &= make_map(enc, mp + o + kMapXM0, x[0], M.sp, M.Lp, xp, bk, 64, BF, S128);
+            ok &= make_map(enc, mp + o + kMapXM1, x[1], M.sp, M.Lp, xp, bk, 64, BF, S128);
+            ok &= make_map(enc, mp + o + kMapA, lo ? M.al : M.ah, M.sp, M.sp, sp2, kBM, bk, BF, SK);
+            ok &= make_map(enc, mp + o + kMapB, lo ? M.bl : M.bh, M.sp, M.sp, sp2, kBM, bk, BF, SK);
         }
         if (P->nsplit == 1) {
-            ok &= make_map(enc, mp + kMapEXF, M.xf, M.sp, M.Lp, (int64_t)M.Lp * 4, 32, 32, true, S128);
-            ok &= make_map(enc, mp + kMapEXH0, M.xh[0], M.sp, M.Lp, xp, 32, 32, false, S64);
-            ok &= make_map(enc, mp + kMapEXH1, M.xh[1], M.sp, M.Lp, xp, 32, 32, false, S64);
-            ok &= make_map(enc, mp + kMapEAF, M.af, M.sp, M.sp, (int64_t)M.sp * 4, 32, 32, true, S128);
-            ok &= make_map(enc, mp + kMapEAH, M.ah, M.sp, M.sp, sp2, 32, 32, false, S64);
-            ok &= make_map(enc, mp + kMapEBH, M.bh, M.sp, M.sp, sp2, 32, 32, false, S64);
+            ok &= make_map(enc, mp + kMapEXQ, M.xq, M.sp, M.Lp, (int64_t)M.Lp, 32, 32, U8,
+                           CU_TENSOR_MAP_SWIZZLE_32B);
+            ok &= make_map(enc, mp + kMapEXH0, M.xh[0], M.sp, M.Lp, xp, 32, 32, BF, S64);
+            ok &= make_map(enc, mp + kMapEXH1, M.xh[1], M.sp, M.Lp, xp, 32, 32, BF, S64);
+            ok &= make_map(enc, mp + kMapEAH, M.ah, M.sp, M.sp, sp2, 32, 32, BF, S64);
+            ok &= make_map(enc, mp + kMapEBH, M.bh, M.sp, M.sp, sp2, 32, 32, BF, S64);
         }
         if (!ok) {
             *err = "cuTensorMapEncodeTiled failed for matrix " + std::to_string(i);
@@ -1391,7 +1461,7 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
         const int esz = (M.io == PE_IO_BF16) ? 2 : 4;
         M.out_tma = 0;
         if (P->nsplit == 1 && reinterpret_cast<uintptr_t>(M.user) % 16 == 0 && (M.ld * esz) % 16 == 0) {
-            M.out_tma = make_map(enc, mp + kMapEOut, M.user, M.m, M.n, M.ld * esz, 32, 32, esz == 4,
+            M.out_tma = make_map(enc, mp + kMapEOut, M.user, M.m, M.n, M.ld * esz, 32, 32, esz == 4 ? F32 : BF,
                                  esz == 4 ? S128 : S64)
                             ? 1
                             : 0;

@@ -40,7 +40,7 @@ struct UmmaPlan {
     int* need2 = nullptr;    // device: per matrix readiness targets of 2-SM plans
     std::vector<TileTask> ph2_t[3];   // 256 x 256 tiles (2-SM plans)
     std::vector<double> ph2_c[3];
-    void* prof = nullptr;    // optional device buffer of 16 int64 per CTA (debug)
+    void* prof = nullptr;    // optional device buffer of 32 int64 per CTA (debug)
     const float* nscale = nullptr;   // device: per-matrix normalisation factors
     // host copy of the per-phase tiles and their costs (for re-scheduling)
     int sms = 0;

@@ -85,12 +85,22 @@ def test_fp32_shapes(m, n):
 @pytest.mark.parametrize("dtype", ["fp32", "bf16", "bf16x3"])
 @pytest.mark.parametrize("m,n", [(200, 333), (333, 200), (128, 256)])
 def test_identity_step(dtype, m, n):
-    """Table (1, 0, 0): the output is the normalised input (prepare + store)."""
+    """Table (1, 0, 0): the output is the normalised input (prepare + store).
+
+    The BF16 path keeps X as its BF16 hi plus a code of the next 8 mantissa
+    bits (x rounded to a 16-bit mantissa), so each element is carried to
+    within 2^-16 |x|; FP32 and BF16x3 keep FP32 X."""
     rng = np.random.default_rng(m + n)
     G = rng.standard_normal((m, n))
     got = run_single(G, [(1.0, 0.0, 0.0)], dtype)
     ref = G.astype(np.float32) / (1.01 * np.linalg.norm(G.astype(np.float32)) + 1e-7)
-    assert np.max(np.abs(got - ref)) <= 1e-6 * np.max(np.abs(ref))
+    if dtype == "bf16":
+        # (+ 2^-20 |x| for the FP32 scaling and norm, + a floor for zeros)
+        assert np.all(np.abs(got - ref) <= (2.0 ** -16 + 2.0 ** -20) * np.abs(ref) + 1e-7 * np.max(np.abs(ref)))
+        # and it is not merely BF16: most elements beat bf16 rounding by far
+        assert np.median(np.abs(got - ref) / np.abs(ref)) < 2.0 ** -14
+    else:
+        assert np.max(np.abs(got - ref)) <= 1e-6 * np.max(np.abs(ref))
 
 
 @pytest.mark.parametrize("dtype", ["fp32", "bf16", "bf16x3"])
