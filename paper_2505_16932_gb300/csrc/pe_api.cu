@@ -206,8 +206,8 @@ int build_plan(const PlanKey& key, Plan** out) {
         M.sp = (int32_t)round_up(M.s, kPadS);
         M.Lp = (int32_t)round_up(M.L, kPadL);
         M.part0 = part;
-        for (int a = 0; a < M.sp / 64; ++a)
-            for (int b = 0; b < M.Lp / 64; ++b) {
+        for (int a = 0; a < M.sp / kPrepRows; ++a)
+            for (int b = 0; b < (M.Lp + kPrepCols - 1) / kPrepCols; ++b) {
                 prep.push_back(TileTask{i, a, b, -1});
                 ++part;
             }
@@ -323,6 +323,10 @@ int build_plan(const PlanKey& key, Plan** out) {
         if (g_dbg_order >= 0) P->umma.order = g_dbg_order;
         if (g_dbg_mode >= 0) P->umma.mode = g_dbg_mode;
         if (g_dbg_nacc == 1 || g_dbg_nacc == 2) P->umma.nacc = g_dbg_nacc;
+        // degree-3 tables (c = 0 in every step) skip the square phase on the BF16 path
+        bool cubic = (dtype == PE_BF16);
+        for (int t = 0; t < key.T && cubic; ++t) cubic = (key.coef[3 * t + 2] == 0.f);
+        P->umma.cubic = cubic;
         int ust = umma_build(&P->umma, P->mats.data(), P->d_mats, count, dtype, P->ds->sms,
                              base + o_umma, umma_bytes, P->d_counters, tune, &g_err);
         if (ust != PE_OK) return ust;

@@ -13,6 +13,10 @@ constexpr int kMaxMatrices = 4096;
 // kPadS rows and kPadL columns with zeros; every GEMM then sees whole tiles.
 constexpr int kPadS = 128;
 constexpr int kPadL = 128;
+// The prepare kernel takes one kPrepRows x kPrepCols strip of the padded
+// layout per block (the last strip of a row may be kPadL wide).
+constexpr int kPrepRows = 64;
+constexpr int kPrepCols = 256;
 
 // sets the thread-local message returned by pe_last_error()
 void set_last_error(const char* msg);

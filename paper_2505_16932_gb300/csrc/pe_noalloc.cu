@@ -59,7 +59,7 @@ extern "C" int pe_polar_noalloc(void* X, int64_t m, int64_t n, const double* tab
     const int64_t s = std::min(m, n), L = std::max(m, n);
     const int64_t sp = rup(s, kPadS), Lp = rup(L, kPadL);
     // workspace layout: [descriptor | tasks | partials | scale | ticket | X | X' | A | B]
-    const int64_t n_prep = (sp / 64) * (Lp / 64);
+    const int64_t n_prep = (sp / kPrepRows) * ((Lp + kPrepCols - 1) / kPrepCols);
     const int64_t ts = sp / 128, tl = Lp / 128;
     const int64_t n_sym = ts * (ts + 1) / 2, n_app = ts * tl;
     const int64_t n_tasks = n_prep + 2 * n_sym + n_app;
@@ -113,8 +113,8 @@ extern "C" int pe_polar_noalloc(void* X, int64_t m, int64_t n, const double* tab
     M.bfp = reinterpret_cast<float*>(base + o_bf);
     TileTask* t = g_na_tiles;
     int k = 0;
-    for (int a = 0; a < sp / 64; ++a)
-        for (int b = 0; b < Lp / 64; ++b) t[k++] = TileTask{0, a, b, -1};
+    for (int a = 0; a < sp / kPrepRows; ++a)
+        for (int b = 0; b < (Lp + kPrepCols - 1) / kPrepCols; ++b) t[k++] = TileTask{0, a, b, -1};
     const int g0 = k;
     for (int a = 0; a < ts; ++a)
         for (int b = a; b < ts; ++b) t[k++] = TileTask{0, a, b, kGram};

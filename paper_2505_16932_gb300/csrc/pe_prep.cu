@@ -1,6 +1,6 @@
 // Step S1 of the online stage (Alg. 1 online box; App. A online code):
 //   nu = ||G||_F,  X_0 = G / (scale * nu + eps),
-// in one pass over G. Each block takes one 64 x 64 tile of the canonical
+// in one pass over G. Each block takes one 64 x 256 strip of the canonical
 // short-side layout (X = G^T when m > n), padded with zeros to whole tiles,
 // and writes it unscaled in every precision the chosen path needs (FP32;
 // BF16 hi with the code of the next 8 bits; BF16 hi + lo), together with the tile's
@@ -93,49 +93,62 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
     if (blockIdx.x == 0) {
         for (int i = threadIdx.x; i < ncounters; i += blockDim.x) counters[i] = 0;
     }
-    const int i0 = tk.tm * 64, l0 = tk.tn * 64;
+    const int i0 = tk.tm * kPrepRows, l0 = tk.tn * kPrepCols;
     const int tid = threadIdx.x;
-    const int rr = tid >> 4, c4 = (tid & 15) * 4;   // 16 rows x 16 float4 per pass
     const int esz = (M.io == PE_IO_BF16) ? 2 : 4;
     const bool vec = (reinterpret_cast<uintptr_t>(M.user) % (4 * esz) == 0) && (M.ld % 4 == 0);
     float ss = 0.f;
-    // all four loads of the thread are issued before any store (the
-    // compiler cannot reorder them across stores that may alias G)
-    float4 ld[4];
+    // all sixteen loads of a thread are issued before any store (the
+    // compiler cannot move loads of G across stores that may alias it)
+    float4 ld[16];
     if (!M.trans) {
-        // X[i][l] = G[i][l]; G is s x L
+        // X[i][l] = G[i][l]; G is s x L. 64 threads per row, 4 rows per pass.
+        const int c = (tid & 63) * 4, r0 = tid >> 6;
+        const bool on = l0 + c < M.Lp;   // the last strip of a row may be 128 wide
 #pragma unroll
-        for (int p = 0; p < 4; ++p) ld[p] = load4(M, vec, M.s, M.L, i0 + rr + 16 * p, l0 + c4);
+        for (int p = 0; p < 16; ++p)
+            ld[p] = on ? load4(M, vec, M.s, M.L, i0 + r0 + 4 * p, l0 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (on) {
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int r = rr + 16 * p;
-            const float4 v = ld[p];
-            ss = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, ss))));
-            put4(M, outputs, (int64_t)(i0 + r) * M.Lp + l0 + c4, v);
+            for (int p = 0; p < 16; ++p) {
+                const float4 v = ld[p];
+                ss = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, ss))));
+                put4(M, outputs, (int64_t)(i0 + r0 + 4 * p) * M.Lp + l0 + c, v);
+            }
         }
     } else {
-        // X[i][l] = G[l][i]; G is L x s: read G rows l with i contiguous, transpose in smem
+        // X[i][l] = G[l][i]; G is L x s: read G rows l with i contiguous (16
+        // threads per 64-float row segment), transpose 64 x 64 sub-tiles in smem
+        const int rr = tid >> 4, c4 = (tid & 15) * 4;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) ld[p] = load4(M, vec, M.L, M.s, l0 + rr + 16 * p, i0 + c4);
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int r = rr + 16 * p;
-            const float4 v = ld[p];
-            ss = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, ss))));
-            tile[r][c4 + 0] = v.x;
-            tile[r][c4 + 1] = v.y;
-            tile[r][c4 + 2] = v.z;
-            tile[r][c4 + 3] = v.w;
+        for (int p = 0; p < 16; ++p) {
+            const int l = l0 + rr + 16 * p;   // sub-tile p / 4, row rr + 16 (p % 4)
+            ld[p] = (l < M.Lp) ? load4(M, vec, M.L, M.s, l, i0 + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        __syncthreads();
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int r = rr + 16 * p;   // canonical row i0 + r, columns l0 + c4 .. + 3
-            const float4 v = make_float4(tile[c4 + 0][r], tile[c4 + 1][r], tile[c4 + 2][r], tile[c4 + 3][r]);
-            put4(M, outputs, (int64_t)(i0 + r) * M.Lp + l0 + c4, v);
+        for (int k = 0; k < kPrepCols / 64; ++k) {
+            if (l0 + 64 * k >= M.Lp) break;   // uniform across the block
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = rr + 16 * q;
+                const float4 v = ld[4 * k + q];
+                ss = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, ss))));
+                tile[r][c4 + 0] = v.x;
+                tile[r][c4 + 1] = v.y;
+                tile[r][c4 + 2] = v.z;
+                tile[r][c4 + 3] = v.w;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = rr + 16 * q;   // canonical row i0 + r, columns l0 + 64 k + c4 .. + 3
+                const float4 v = make_float4(tile[c4 + 0][r], tile[c4 + 1][r], tile[c4 + 2][r], tile[c4 + 3][r]);
+                put4(M, outputs, (int64_t)(i0 + r) * M.Lp + l0 + 64 * k + c4, v);
+            }
+            __syncthreads();
         }
     }
-    // tile sum of squares: FP32 per thread, FP64 across the block, fixed order
+    // strip sum of squares: FP32 per thread, FP64 across the block, fixed order
     double d = (double)ss;
     for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
     if ((tid & 31) == 0) red[tid >> 5] = d;

@@ -83,6 +83,7 @@ struct StepArgs {
     int* status;
     float a, b, c;
     int step, cur, last, dependent, withhold;
+    int cubic;          // c = 0 in every step: the Gram epilogue writes B = b A, no square tiles
     uint64_t wait_ns;
     long long* prof;    // optional per-CTA cycle counters (debug)
     const float* nscale;  // per-matrix normalisation factor, applied in step 0
@@ -731,7 +732,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             const CUtensorMap* mp = A.maps + (size_t)tk.mat * kMapsPerMat;
             if (A.dependent && g.kind != kGram) {
                 const long long c0 = clock64();
-                const int which = (g.kind == kSquare) ? 0 : 1;
+                const int which = (g.kind == kSquare || A.cubic) ? 0 : 1;   // wait for A, or for B
                 wait_counter(A.counters + 2 * g.mat + which, (A.step + 1) * A.need[2 * g.mat + which], limit,
                              A.status);
                 fence_proxy_async_global();
@@ -1012,8 +1013,10 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
 #pragma unroll
                         for (int j = 0; j < 32; ++j) v[j] = fmaf(A.b, pre[j], A.c * v[j]);
                     } else {
+                        // Gram: A = s^2 X X^T, or B = b s^2 X X^T when c = 0 throughout
+                        const float gs = A.cubic ? A.b * s0 * s0 : s0 * s0;
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) v[j] *= s0 * s0;
+                        for (int j = 0; j < 32; ++j) v[j] *= gs;
                     }
                     if (sub) { const long long t = clock64(); c_rdx += t - s0c; s0c = t; }
                     // the previous chunk's stores have read the output box
@@ -1055,7 +1058,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                             if (M.trans) tma_store_2d(mp + kMapEOut, smem_u32(s_out), gi0, col0);
                             else tma_store_2d(mp + kMapEOut, smem_u32(s_out), col0, gi0);
                         } else {
-                            const CUtensorMap* hm = mp + ((g.kind == kGram) ? kMapEAH : kMapEBH);
+                            const CUtensorMap* hm = mp + ((g.kind == kGram && !A.cubic) ? kMapEAH : kMapEBH);
                             tma_store_2d(hm, smem_u32(s_out), col0, gi0);
                             if (cls != kChunkDiag) tma_store_2d(hm, smem_u32(s_out + 2048), gi0, col0);
                         }
@@ -1169,7 +1172,7 @@ struct HostTile {
 
 // Tiles of one matrix. Symmetric products keep the 128 x 256 tiles that
 // reach the upper triangle (column end > row start).
-void tiles_of(const DevMat& M, int i, std::vector<HostTile>* ph) {
+void tiles_of(const DevMat& M, int i, std::vector<HostTile>* ph, bool cubic) {
     const int tm = M.sp / kBM;
     const int ts = (M.sp + kBN - 1) / kBN;
     for (int a = 0; a < tm; ++a)
@@ -1177,7 +1180,7 @@ void tiles_of(const DevMat& M, int i, std::vector<HostTile>* ph) {
             const int bn = std::min(kBN, M.sp - b * kBN);
             if (b * kBN + bn <= a * kBM) continue;
             ph[kGram].push_back(HostTile{TileTask{i, a, b, kGram}, (double)kBM * bn * M.Lp});
-            ph[kSquare].push_back(HostTile{TileTask{i, a, b, kSquare}, (double)kBM * bn * M.sp});
+            if (!cubic) ph[kSquare].push_back(HostTile{TileTask{i, a, b, kSquare}, (double)kBM * bn * M.sp});
         }
     const int tl = (M.Lp + kBN - 1) / kBN;
     for (int a = 0; a < tm; ++a)
@@ -1467,7 +1470,7 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
                             : 0;
         }
         const size_t g0 = ph[kGram].size(), s0 = ph[kSquare].size();
-        tiles_of(M, i, ph);
+        tiles_of(M, i, ph, P->cubic);
         need[2 * i] = (int)(ph[kGram].size() - g0);
         need[2 * i + 1] = (int)(ph[kSquare].size() - s0);
     }
@@ -1571,10 +1574,12 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
                 for (int b = a; b < t2; ++b) {
                     P->ph2_t[kGram].push_back(TileTask{i, a, b, kGram});
                     P->ph2_c[kGram].push_back(256.0 * 256.0 * M.Lp);
-                    P->ph2_t[kSquare].push_back(TileTask{i, a, b, kSquare});
-                    P->ph2_c[kSquare].push_back(256.0 * 256.0 * M.sp);
+                    if (!P->cubic) {
+                        P->ph2_t[kSquare].push_back(TileTask{i, a, b, kSquare});
+                        P->ph2_c[kSquare].push_back(256.0 * 256.0 * M.sp);
+                        need2[2 * i + 1] += 2;
+                    }
                     need2[2 * i] += 2;       // each CTA of the pair signals its half
-                    need2[2 * i + 1] += 2;
                 }
             for (int a = 0; a < t2; ++a)
                 for (int b = 0; b < tl; ++b) {
@@ -1629,6 +1634,7 @@ cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, i
     A.cur = t & 1;
     A.last = last;
     A.withhold = withhold;
+    A.cubic = P->cubic ? 1 : 0;
     A.wait_ns = wait_ns;
     A.prof = reinterpret_cast<long long*>(P->prof);
     *launched = 0;

@@ -234,16 +234,27 @@ def test_graph_replay_repeats():
         assert torch.equal(X, F)
 
 
+# BF16 on iid Gaussian inputs run well past convergence: the a X term uses
+# the 16-bit-mantissa master while B X uses its BF16 rounding X_b, so each
+# converged step adds -B (X - X_b) ~ (a_t - 1) 2^-9 / sqrt(3) |X| of rotation
+# error that later steps do not damp; with the T = 6, l = 1e-3 table this sums
+# to ~2.4e-2 on such inputs (2.39e-2 measured in a CPU emulation of the same
+# arithmetic), against 4-5e-3 on the heavy-tailed spectra of the Muon
+# workloads. The bar for this case is that bound rounded up; BF16x3, whose
+# update is compensated, keeps the 2e-2 bar.
+BF16_TOL_GAUSS_CONVERGED = 3e-2
+
+
 def test_batched_vs_oracle_uneven():
     mats = _uneven(seed=9)
     tab = table(1e-3, 6)
-    for dtype, tol in (("fp32", FP32_TOL), ("bf16", BF16_TOL)):
+    for dtype, tol in (("fp32", FP32_TOL), ("bf16", BF16_TOL_GAUSS_CONVERGED), ("bf16x3", BF16_TOL)):
         Xs = [to_dev(G) for G in mats]
         pe.pe_polar_batched(Xs, tab, dtype)
         pe.pe_sync_status()
         for X, G in zip(Xs, mats):
             ref = O.polar_express(G.astype(np.float32).astype(np.float64), tab)
-            assert O.rel_fro(X.cpu().numpy().astype(np.float64), ref) <= (tol if dtype == "fp32" else 3e-2)
+            assert O.rel_fro(X.cpu().numpy().astype(np.float64), ref) <= tol, (dtype, G.shape)
 
 
 # ---------------------------------------------------- status / failures
@@ -278,7 +289,7 @@ def test_readiness_wait_timeout_reports_status():
     pe.pe_polar_batched(Xs, tab, "bf16")
     pe.pe_sync_status()
     ref = O.polar_express(mats[1].astype(np.float32).astype(np.float64), tab)
-    assert O.rel_fro(Xs[1].cpu().numpy().astype(np.float64), ref) <= 3e-2
+    assert O.rel_fro(Xs[1].cpu().numpy().astype(np.float64), ref) <= BF16_TOL
 
 
 def test_injected_alloc_failure():
@@ -327,3 +338,27 @@ def test_kblock_and_order_variants_bitwise(dtype):
     for o in outs[1:]:
         for a, b in zip(outs[0], o):
             assert torch.equal(a, b)
+
+
+# ------------------------------------------------ degree-3 tables (c = 0)
+
+@pytest.mark.parametrize("which", ["pe3", "ns3"])
+def test_degree3_tables_skip_square(which):
+    """Degree-3 tables (the degree-3 greedy composition of Thm. 1, and the
+    Newton-Schulz cubic) have c = 0 in every row: the BF16 path writes
+    B = b A from the Gram epilogue and launches no square tiles. Uneven batch,
+    fused, phased and 2-SM-eligible shapes, against the FP64 iteration."""
+    if which == "pe3":
+        tab = pe.pe_coeffs(3, 1e-3, 8, 1.01)
+    else:
+        tab = np.array([[1.5, -0.5, 0.0]] * 12)
+    assert np.all(tab[:, 2] == 0.0)
+    mats = _uneven(seed=5) + _even(seed=6)[:3]
+    for dtype, tol in (("fp32", FP32_TOL), ("bf16", BF16_TOL)):
+        for flags in (0, pe.PE_BATCH_PHASED):
+            Xs = [to_dev(G) for G in mats]
+            pe.pe_polar_batched(Xs, tab, dtype, flags=flags)
+            pe.pe_sync_status()
+            for X, G in zip(Xs, mats):
+                ref = O.polar_express(G.astype(np.float32).astype(np.float64), tab)
+                assert O.rel_fro(X.cpu().numpy().astype(np.float64), ref) <= tol, (dtype, flags, G.shape)
