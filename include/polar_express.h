@@ -286,6 +286,62 @@ int pe_debug_set(int key, int64_t value);
  */
 int pe_polar_noalloc(void* X, int64_t m, int64_t n, const double* table, int T, void* stream);
 
+/* ------------------------------------------------ long-side split (ranks)
+ *
+ * One matrix too large for one GPU, cut along its long side over R ranks
+ * (the multi-device form of Alg. 1's online stage with A on the short side):
+ * rank r holds G_r, the block of L_r of the L long-side columns (or rows) of
+ * G, with the short side s shared. Then
+ *   ||G||_F^2 = sum_r ||G_r||_F^2,   A = X X^T = sum_r X_r X_r^T,
+ * B = b A + c A^2 is the same on every rank, and X_r <- a X_r + B X_r is
+ * local: the iteration needs one all-reduce of a scalar before the first
+ * step and one all-reduce of the s x s FP32 Gram per step, and nothing else.
+ * The library computes every rank-local part; the caller performs the two
+ * sums (e.g. NCCL all-reduce through torch.distributed) between the calls.
+ *
+ * Sequence on each rank, all on `stream`:
+ *   pe_split_open -> pe_split_sumsq -> [sum over ranks] -> pe_split_set_norm
+ *   -> for t = 0 .. T-1: pe_split_gram(t) -> [sum A over ranks] -> pe_split_step(t)
+ *   -> pe_split_close.
+ * pe_split_step(T - 1) writes the rank's block of the result into X.
+ * With R = 1 the results are those of pe_polar_batched_ex with
+ * PE_BATCH_PHASED | PE_BATCH_NO_GRAPH.
+ */
+typedef struct pe_split_s* pe_split_t;
+
+/* X: the rank's block, rows x cols row-major (ld = cols), FP32, device
+ * memory, in/out (read by pe_split_sumsq, overwritten by the last step).
+ * short_is_rows = 1: the short side s = rows is shared and the ranks split
+ * the columns (X_r = G_r); 0: s = cols is shared and the ranks split the
+ * rows (X_r = G_r^T). Either local extent may be smaller than s.
+ * table, T, dtype as for pe_polar (PE_FP32 or PE_BF16). The handle owns its
+ * workspace until pe_split_close. Errors: PE_EINVAL, PE_ENOMEM, PE_ECUDA,
+ * PE_EUNSUPPORTED (PE_BF16X3). */
+int pe_split_open(void* X, int64_t rows, int64_t cols, int short_is_rows, const double* table, int T,
+                  int dtype, void* stream, pe_split_t* handle);
+
+/* Prepares the rank's block (cast, orientation, padding) and returns its
+ * squared Frobenius norm in *sumsq (FP64, summed in a fixed order). Waits
+ * for the stream. */
+int pe_split_sumsq(pe_split_t handle, double* sumsq);
+
+/* Sets the normalisation from the sum over ranks of pe_split_sumsq:
+ * X_0 = G / (1.01 sqrt(total) + 1e-7) (Alg. 1; App. A constants). */
+int pe_split_set_norm(pe_split_t handle, double total_sumsq);
+
+/* The rank's partial Gram of step t (t = 0 .. T-1, in order), X_r X_r^T, as
+ * a full symmetric s x s FP32 matrix into A (device memory, row-major,
+ * leading dimension lda >= s). Step 0 includes the normalisation. */
+int pe_split_gram(pe_split_t handle, int t, float* A, int64_t lda);
+
+/* Step t given A = sum over ranks of the partial Grams (device memory, s x s
+ * FP32, lda >= s): B = b_t A + c_t A^2, X_r <- a_t X_r + B X_r; the last step
+ * writes X. */
+int pe_split_step(pe_split_t handle, int t, const float* A, int64_t lda);
+
+/* Frees the handle's workspace (after the stream's work has finished). */
+int pe_split_close(pe_split_t handle);
+
 #ifdef __cplusplus
 }
 #endif

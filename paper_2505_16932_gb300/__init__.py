@@ -80,6 +80,12 @@ def lib() -> ctypes.CDLL:
         "pe_debug_set": (c_i, [c_i, c_i64]),
         "pe_trace_enable": (c_i, [c_i]),
         "pe_trace_read": (c_i, [P_i64, P_d, c_i]),
+        "pe_split_open": (c_i, [c_p, c_i64, c_i64, c_i, P_d, c_i, c_i, c_p, ctypes.POINTER(c_p)]),
+        "pe_split_sumsq": (c_i, [c_p, P_d]),
+        "pe_split_set_norm": (c_i, [c_p, c_d]),
+        "pe_split_gram": (c_i, [c_p, c_i, c_p, c_i64]),
+        "pe_split_step": (c_i, [c_p, c_i, c_p, c_i64]),
+        "pe_split_close": (c_i, [c_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -234,3 +240,57 @@ def pe_debug_set(key: int, value: int):
 
 def pe_version() -> int:
     return int(lib().pe_version())
+
+
+# ------------------------------------------------------ long-side split
+
+class Split:
+    """One rank's block of a matrix split along its long side (pe_split_*).
+
+    ``X``: the rank's block, a contiguous 2-D float32 CUDA tensor, in/out.
+    ``short_is_rows``: True when the shared short side is X's rows (ranks
+    hold column blocks), False when it is X's columns (ranks hold row
+    blocks). The caller sums ``sumsq()`` and every ``gram`` result over the
+    ranks; see shard.polar_split_long for the whole sequence."""
+
+    def __init__(self, X, short_is_rows: bool, table, dtype: str = "bf16", stream=None):
+        _check_tensor(X)
+        if not X.is_contiguous() or _io_of(X) != PE_IO_FP32:
+            raise PolarExpressError(PE_EINVAL, "the split block must be a contiguous float32 tensor")
+        self.X = X
+        self.table = _table(table)
+        self.T = self.table.shape[0]
+        self.s = X.shape[0] if short_is_rows else X.shape[1]
+        self._stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        _check(lib().pe_split_open(ctypes.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], int(bool(short_is_rows)),
+                                   _dptr(self.table), self.T, DTYPES[dtype], ctypes.c_void_p(self._stream),
+                                   ctypes.byref(h)))
+        self._h = h
+
+    def sumsq(self) -> float:
+        out = ctypes.c_double()
+        _check(lib().pe_split_sumsq(self._h, ctypes.byref(out)))
+        return out.value
+
+    def set_norm(self, total_sumsq: float):
+        _check(lib().pe_split_set_norm(self._h, float(total_sumsq)))
+
+    def _a(self, A):
+        _check_tensor(A)
+        if _io_of(A) != PE_IO_FP32 or A.shape[0] < self.s or A.shape[1] < self.s:
+            raise PolarExpressError(PE_EINVAL, "A must be a float32 CUDA tensor of at least s x s")
+        return ctypes.c_void_p(A.data_ptr()), A.stride(0)
+
+    def gram(self, t: int, A):
+        p, lda = self._a(A)
+        _check(lib().pe_split_gram(self._h, int(t), p, lda))
+
+    def step(self, t: int, A):
+        p, lda = self._a(A)
+        _check(lib().pe_split_step(self._h, int(t), p, lda))
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _check(lib().pe_split_close(self._h))
+        self._h = None

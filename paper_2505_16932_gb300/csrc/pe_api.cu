@@ -120,6 +120,10 @@ int device_state(DeviceState** out) {
 
 // ------------------------------------------------------------------ plans
 
+// internal plan flags (above the public PE_BATCH_* bits)
+constexpr unsigned kFlagSplit = 1u << 16;           // long-side split plan (pe_split_*)
+constexpr unsigned kFlagSplitShortCols = 1u << 17;  // split plan whose shared short side is the columns
+
 struct PlanKey {
     int dev, dtype, T, io, count;
     unsigned flags;
@@ -203,6 +207,13 @@ int build_plan(const PlanKey& key, Plan** out) {
         M.io = key.io;
         M.s = (int32_t)std::min(m, n);
         M.L = (int32_t)std::max(m, n);
+        if (key.flags & kFlagSplit) {
+            // long-side split: the shared short side is fixed by the caller,
+            // the local long extent may be the smaller one
+            M.trans = (key.flags & kFlagSplitShortCols) ? 1 : 0;
+            M.s = (int32_t)(M.trans ? n : m);
+            M.L = (int32_t)(M.trans ? m : n);
+        }
         M.sp = (int32_t)round_up(M.s, kPadS);
         M.Lp = (int32_t)round_up(M.L, kPadL);
         M.part0 = part;
@@ -226,6 +237,7 @@ int build_plan(const PlanKey& key, Plan** out) {
             o.ah = cv.take(2 * ss);
             o.bh = cv.take(2 * ss);
             if (dtype == PE_BF16) o.xq = cv.take(sL);
+            if (dtype == PE_BF16 && (key.flags & kFlagSplit)) o.af = cv.take(4 * ss);   // partial Gram, FP32
             if (dtype == PE_BF16X3) {
                 o.xf = cv.take(4 * sL);
                 o.af = cv.take(4 * ss);
@@ -291,6 +303,7 @@ int build_plan(const PlanKey& key, Plan** out) {
             M.ah = reinterpret_cast<bf16*>(base + o.ah);
             M.bh = reinterpret_cast<bf16*>(base + o.bh);
             if (dtype == PE_BF16) M.xq = reinterpret_cast<int8_t*>(base + o.xq);
+            if (dtype == PE_BF16 && (key.flags & kFlagSplit)) M.af = reinterpret_cast<float*>(base + o.af);
             if (dtype == PE_BF16X3) {
                 M.xf = reinterpret_cast<float*>(base + o.xf);
                 M.af = reinterpret_cast<float*>(base + o.af);
@@ -324,7 +337,12 @@ int build_plan(const PlanKey& key, Plan** out) {
         if (g_dbg_mode >= 0) P->umma.mode = g_dbg_mode;
         if (g_dbg_nacc == 1 || g_dbg_nacc == 2) P->umma.nacc = g_dbg_nacc;
         // degree-3 tables (c = 0 in every step) skip the square phase on the BF16 path
-        bool cubic = (dtype == PE_BF16);
+        bool cubic = (dtype == PE_BF16) && !(key.flags & kFlagSplit);   // the split exchanges A itself
+        P->umma.gram_f32 = (key.flags & kFlagSplit) != 0;
+        if (P->umma.gram_f32) {
+            P->umma.mode = 0;
+            P->umma.bk = 64;
+        }
         for (int t = 0; t < key.T && cubic; ++t) cubic = (key.coef[3 * t + 2] == 0.f);
         P->umma.cubic = cubic;
         int ust = umma_build(&P->umma, P->mats.data(), P->d_mats, count, dtype, P->ds->sms,
@@ -607,11 +625,163 @@ int run(void* const* X, const int64_t* m, const int64_t* n, const int64_t* ld, i
     return PE_OK;
 }
 
+// ------------------------------------------------------ long-side split
+// One rank's block of a matrix split along its long side (pe_split_*): a
+// dedicated single-matrix plan (orientation fixed by the caller, phased
+// launches, no graph, no tuning), stepped by the host one phase at a time so
+// that the caller can sum the partial norms and Grams across ranks.
+
+struct Split {
+    std::unique_ptr<Plan> plan;
+    cudaStream_t st = nullptr;
+    int s = 0;             // shared short side
+    float s0 = 0.f;        // normalisation factor from the global norm
+    bool norm_set = false;
+    int next_gram = 0, next_step = 0;
+    std::vector<double> partials;
+};
+
+int split_open(void* X, int64_t rows, int64_t cols, int short_is_rows, const double* table, int T, int dtype,
+               void* stream, Split** out) {
+    if (!out) return fail(PE_EINVAL, "handle pointer is NULL");
+    *out = nullptr;
+    if (!X || !table) return fail(PE_EINVAL, "NULL argument");
+    if (dtype == PE_BF16X3) return fail(PE_EUNSUPPORTED, "the long-side split supports PE_FP32 and PE_BF16");
+    if (dtype != PE_FP32 && dtype != PE_BF16) return fail(PE_EINVAL, "bad dtype");
+    if (T < 1 || T > kMaxSteps) return fail(PE_EINVAL, "T must be in 1..64");
+    if (rows < 1 || cols < 1) return fail(PE_EINVAL, "sizes must be >= 1");
+    if (rows > (1 << 20) || cols > (1 << 20) || rows * cols > (int64_t)1 << 31)
+        return fail(PE_EINVAL, "matrix too large (rows, cols <= 2^20, rows*cols <= 2^31)");
+    if (reinterpret_cast<uintptr_t>(X) % 4) return fail(PE_EINVAL, "misaligned matrix pointer");
+    PlanKey key;
+    key.dtype = dtype;
+    key.T = T;
+    key.io = PE_IO_FP32;
+    key.count = 1;
+    key.flags = kFlagSplit | (short_is_rows ? 0u : kFlagSplitShortCols) | PE_BATCH_NO_GRAPH | PE_BATCH_PHASED |
+                PE_BATCH_NO_TUNE;
+    key.scale = 1.01f;
+    key.eps = 1e-7f;
+    key.ptrs = {reinterpret_cast<uintptr_t>(X)};
+    key.dims = {rows, cols, cols};
+    key.coef.resize(3 * T);
+    for (int i = 0; i < 3 * T; ++i) {
+        if (!std::isfinite(table[i])) return fail(PE_EINVAL, "non-finite coefficient in table");
+        key.coef[i] = (float)table[i];
+    }
+    PE_CU(cudaGetDevice(&key.dev));
+    Plan* p = nullptr;
+    int r = build_plan(key, &p);
+    if (r != PE_OK) return r;
+    auto S = std::make_unique<Split>();
+    S->plan.reset(p);
+    S->st = reinterpret_cast<cudaStream_t>(stream);
+    S->s = p->mats[0].s;
+    *out = S.release();
+    return PE_OK;
+}
+
+int split_sumsq(Split* S, double* sumsq) {
+    if (!S || !sumsq) return fail(PE_EINVAL, "NULL argument");
+    Plan* P = S->plan.get();
+    const PlanKey& k = P->key;
+    const int outputs = (k.dtype == PE_BF16) ? kPrepCode : kPrepF32;
+    PE_CU(launch_prepare(P->d_mats, 1, P->d_prep, P->n_prep, P->d_partials, k.scale, k.eps, outputs,
+                         P->d_nscale, P->ds->status, P->d_counters, P->n_counters, P->d_ticket, S->st));
+    S->partials.resize(P->n_prep);
+    PE_CU(cudaMemcpyAsync(S->partials.data(), P->d_partials, sizeof(double) * P->n_prep, cudaMemcpyDeviceToHost,
+                          S->st));
+    PE_CU(cudaStreamSynchronize(S->st));
+    // the order of the single-device normalisation: 32 strided lane sums,
+    // then the butterfly that leaves lane 0 with the total
+    double lanes[32];
+    for (int l = 0; l < 32; ++l) {
+        lanes[l] = 0.0;
+        for (size_t i = l; i < S->partials.size(); i += 32) lanes[l] += S->partials[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        double nxt[32];
+        for (int l = 0; l < 32; ++l) nxt[l] = lanes[l] + lanes[l ^ o];
+        for (int l = 0; l < 32; ++l) lanes[l] = nxt[l];
+    }
+    *sumsq = lanes[0];
+    S->norm_set = false;
+    S->next_gram = S->next_step = 0;
+    return PE_OK;
+}
+
+int split_set_norm(Split* S, double total) {
+    if (!S) return fail(PE_EINVAL, "NULL handle");
+    if (!(std::isfinite(total) && total >= 0)) return fail(PE_EINVAL, "total_sumsq must be finite and >= 0");
+    Plan* P = S->plan.get();
+    S->s0 = (float)(1.0 / ((double)P->key.scale * std::sqrt(total) + (double)P->key.eps));
+    PE_CU(cudaMemcpyAsync(P->d_nscale, &S->s0, sizeof(float), cudaMemcpyHostToDevice, S->st));
+    S->norm_set = true;
+    return PE_OK;
+}
+
+int split_gram(Split* S, int t, float* A, int64_t lda) {
+    if (!S || !A) return fail(PE_EINVAL, "NULL argument");
+    Plan* P = S->plan.get();
+    const PlanKey& k = P->key;
+    if (!S->norm_set) return fail(PE_EINVAL, "pe_split_set_norm must come before the first Gram");
+    if (t != S->next_gram || t != S->next_step || t >= k.T)
+        return fail(PE_EINVAL, "steps must run in order: gram(t) then step(t), t = 0 .. T-1");
+    if (lda < S->s) return fail(PE_EINVAL, "lda must be >= s");
+    const DevMat& M = P->mats[0];
+    const float a = k.coef[3 * t], b = k.coef[3 * t + 1], c = k.coef[3 * t + 2];
+    if (k.dtype == PE_FP32) {
+        PE_CU(launch_simt_phase(P->d_mats, P->d_tiles[kGram], P->n_tiles[kGram], kGram, a, b, c, t & 1, 0, t == 0,
+                                P->d_nscale, S->st));
+    } else {
+        int nl = 0;
+        cudaError_t e = umma_step(&P->umma, t, a, b, c, 0, kGram, -1, (uint64_t)g_dbg_wait_ns, P->ds->status,
+                                  S->st, &nl);
+        if (e != cudaSuccess) return cuda_fail(e, "umma_step (split Gram)");
+    }
+    PE_CU(cudaMemcpy2DAsync(A, sizeof(float) * lda, M.af, sizeof(float) * M.sp, sizeof(float) * S->s, S->s,
+                            cudaMemcpyDeviceToDevice, S->st));
+    S->next_gram = t + 1;
+    return PE_OK;
+}
+
+int split_step(Split* S, int t, const float* A, int64_t lda) {
+    if (!S || !A) return fail(PE_EINVAL, "NULL argument");
+    Plan* P = S->plan.get();
+    const PlanKey& k = P->key;
+    if (t != S->next_step || S->next_gram != t + 1) return fail(PE_EINVAL, "pe_split_gram(t) must come before pe_split_step(t)");
+    if (lda < S->s) return fail(PE_EINVAL, "lda must be >= s");
+    const DevMat& M = P->mats[0];
+    const float a = k.coef[3 * t], b = k.coef[3 * t + 1], c = k.coef[3 * t + 2];
+    const int last = (t == k.T - 1);
+    if (k.dtype == PE_FP32) {
+        PE_CU(cudaMemcpy2DAsync(M.af, sizeof(float) * M.sp, A, sizeof(float) * lda, sizeof(float) * S->s, S->s,
+                                cudaMemcpyDeviceToDevice, S->st));
+        for (int ph = kSquare; ph <= kApply; ++ph)
+            PE_CU(launch_simt_phase(P->d_mats, P->d_tiles[ph], P->n_tiles[ph], ph, a, b, c, t & 1, last, t == 0,
+                                    P->d_nscale, S->st));
+    } else {
+        PE_CU(launch_split_load_a(A, lda, S->s, M.sp, M.ah, S->st));
+        for (int ph = kSquare; ph <= kApply; ++ph) {
+            int nl = 0;
+            cudaError_t e = umma_step(&P->umma, t, a, b, c, last, ph, -1, (uint64_t)g_dbg_wait_ns, P->ds->status,
+                                      S->st, &nl);
+            if (e != cudaSuccess) return cuda_fail(e, "umma_step (split step)");
+        }
+    }
+    S->next_step = t + 1;
+    return PE_OK;
+}
+
 }  // namespace
 
 void set_last_error(const char* msg) { g_err = msg; }
 
 }  // namespace pe
+
+struct pe_split_s {
+    pe::Split* impl;
+};
 
 extern "C" {
 
@@ -711,6 +881,48 @@ void pe_release(void) {
     std::lock_guard<std::mutex> lk(pe::g_mu);
     if (!pe::g_plans.empty()) cudaDeviceSynchronize();
     pe::g_plans.clear();
+}
+
+int pe_split_open(void* X, int64_t rows, int64_t cols, int short_is_rows, const double* table, int T, int dtype,
+                  void* stream, pe_split_t* handle) {
+    std::lock_guard<std::mutex> lk(pe::g_mu);
+    if (!handle) return pe::fail(PE_EINVAL, "handle pointer is NULL");
+    *handle = nullptr;
+    pe::Split* S = nullptr;
+    int r = pe::split_open(X, rows, cols, short_is_rows, table, T, dtype, stream, &S);
+    if (r != PE_OK) return r;
+    *handle = new pe_split_s{S};
+    return PE_OK;
+}
+
+int pe_split_sumsq(pe_split_t h, double* sumsq) {
+    std::lock_guard<std::mutex> lk(pe::g_mu);
+    return pe::split_sumsq(h ? h->impl : nullptr, sumsq);
+}
+
+int pe_split_set_norm(pe_split_t h, double total_sumsq) {
+    std::lock_guard<std::mutex> lk(pe::g_mu);
+    return pe::split_set_norm(h ? h->impl : nullptr, total_sumsq);
+}
+
+int pe_split_gram(pe_split_t h, int t, float* A, int64_t lda) {
+    std::lock_guard<std::mutex> lk(pe::g_mu);
+    return pe::split_gram(h ? h->impl : nullptr, t, A, lda);
+}
+
+int pe_split_step(pe_split_t h, int t, const float* A, int64_t lda) {
+    std::lock_guard<std::mutex> lk(pe::g_mu);
+    return pe::split_step(h ? h->impl : nullptr, t, A, lda);
+}
+
+int pe_split_close(pe_split_t h) {
+    std::lock_guard<std::mutex> lk(pe::g_mu);
+    if (!h) return pe::fail(PE_EINVAL, "NULL handle");
+    cudaError_t e = cudaStreamSynchronize(h->impl->st);
+    delete h->impl;
+    delete h;
+    if (e != cudaSuccess) return pe::cuda_fail(e, "cudaStreamSynchronize");
+    return PE_OK;
 }
 
 int pe_debug_set(int key, int64_t value) {

@@ -111,6 +111,7 @@ __device__ __forceinline__ float x_join(uint32_t hi32, uint32_t cw, int k) {
 cudaError_t launch_prepare(const DevMat* mats, int nmats, const TileTask* tiles, int ntiles, double* partials,
                            float scale, float eps, int outputs, float* nscale, int* status, int* counters,
                            int ncounters, unsigned* ticket, cudaStream_t st);
+cudaError_t launch_split_load_a(const float* A, int64_t lda, int s, int sp, bf16* ah, cudaStream_t st);
 cudaError_t launch_simt_phase(const DevMat* mats, const TileTask* tiles, int ntiles, int kind,
                               float a, float b, float c, int src, int last, int first,
                               const float* nscale, cudaStream_t st);

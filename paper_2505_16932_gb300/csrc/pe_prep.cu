@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "pe_internal.h"
 
 namespace pe {
@@ -173,7 +175,9 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
             const double nu = sqrt(s);
-            const double den = (double)scale * nu + (double)eps;
+            // separate rounded multiply and add (no contraction), so that the
+            // host computes the same value from the same sum (pe_split_set_norm)
+            const double den = __dadd_rn(__dmul_rn((double)scale, nu), (double)eps);
             float inv = (float)(1.0 / den);
             if (!isfinite(nu) || !(den > 0.0)) {
                 atomicOr(status, 2);
@@ -186,7 +190,25 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
     if (tid == 0) *ticket = 0u;
 }
 
+// Long-side split: the summed FP32 Gram (s x s, leading dimension lda) into
+// the padded BF16 operand A (sp x sp, zero outside s x s).
+__global__ void __launch_bounds__(256) split_load_a_kernel(const float* __restrict__ A, int64_t lda, int s, int sp,
+                                                           bf16* __restrict__ ah) {
+    const int64_t n = (int64_t)sp * sp;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k / sp), j = (int)(k % sp);
+        ah[k] = __float2bfloat16_rn((i < s && j < s) ? A[(int64_t)i * lda + j] : 0.f);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_split_load_a(const float* A, int64_t lda, int s, int sp, bf16* ah, cudaStream_t st) {
+    const int64_t n = (int64_t)sp * sp;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    split_load_a_kernel<<<blocks, 256, 0, st>>>(A, lda, s, sp, ah);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_prepare(const DevMat* mats, int nmats, const TileTask* tiles, int ntiles, double* partials,
                            float scale, float eps, int outputs, float* nscale, int* status, int* counters,

@@ -643,7 +643,9 @@ enum ProfSlot {
 // even CTA issues the MMAs (M = 256), each CTA loads its half of A and B and
 // reads its 128 accumulator rows from its own TMEM. NACC accumulators of 256
 // columns are allocated (two give epilogue / MMA overlap).
-template <int NS, int BK, int MODE, int NACC>
+// GF32: the long-side split's kernel, whose Gram writes the full FP32 A
+// (DevMat::af); a separate instantiation keeps that path out of the others.
+template <int NS, int BK, int MODE, int NACC, bool GF32 = false>
 __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_constant__ StepArgs A) {
     using C = Cfg<NS, BK, MODE>;
     constexpr bool MC = (MODE == 1);
@@ -1019,6 +1021,26 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                         for (int j = 0; j < 32; ++j) v[j] *= gs;
                     }
                     if (sub) { const long long t = clock64(); c_rdx += t - s0c; s0c = t; }
+                    if (GF32 && g.kind == kGram) {
+                        // partial Gram of a long-side split: full symmetric FP32 A,
+                        // row segment of this lane plus (coalesced) mirror columns
+                        float* af = M.af;
+                        if (cls == kChunkDiag) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const int gj = col0 + j;
+                                if (gj >= gi) af[(int64_t)gi * M.sp + gj] = v[j];
+                                if (gj > gi) af[(int64_t)gj * M.sp + gi] = v[j];
+                            }
+                        } else {
+                            float4* row = reinterpret_cast<float4*>(af + (int64_t)gi * M.sp + col0);
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) row[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) af[(int64_t)(col0 + j) * M.sp + gi] = v[j];
+                        }
+                        continue;
+                    }
                     // the previous chunk's stores have read the output box
                     if (lane == 0) bulk_wait_read0();
                     __syncwarp();
@@ -1527,6 +1549,9 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(umma_step_kernel<1, 64, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Cfg<1, 64>::kSmem);
+    if (e == cudaSuccess && P->gram_f32)
+        e = cudaFuncSetAttribute(umma_step_kernel<1, 64, 0, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Cfg<1, 64>::kSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(umma_step_kernel<3, 64, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Cfg<3, 64>::kSmem);
@@ -1664,6 +1689,7 @@ cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, i
             if (P->bk == 64) return cudaLaunchKernelEx(&cfg, umma_step_kernel<3, 64, 0, 2>, A);
             return cudaLaunchKernelEx(&cfg, umma_step_kernel<3, 32, 0, 2>, A);
         }
+        if (P->gram_f32) return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64, 0, 2, true>, A);
         if (P->mode == 2) {
             if (P->nacc == 2) return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64, 2, 2>, A);
             return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64, 2, 1>, A);

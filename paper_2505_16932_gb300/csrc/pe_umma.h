@@ -36,6 +36,8 @@ struct UmmaPlan {
     int nacc = 2;            // accumulators per CTA in mode 2 (1 or 2)
     bool cubic = false;      // every step has c = 0 (BF16 only): B = b A comes from the
                              // Gram epilogue and there are no square tiles
+    bool gram_f32 = false;   // long-side split: the Gram writes the full FP32 A into DevMat::af
+                             // (its own kernel instantiation; mode 0, 64-wide k-blocks)
     int max_clusters = 0;    // co-resident clusters of two, multicast kernel (0: unavailable)
     int max_clusters2 = 0;   // co-resident clusters of two, 2-SM kernel (0: unavailable)
     size_t smem_bytes2 = 0;  // dynamic shared memory of the 2-SM kernel

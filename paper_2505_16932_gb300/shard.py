@@ -1,11 +1,18 @@
-"""Multi-GPU form of pe_polar_batched: one model's Muon matrices over ranks.
+"""Multi-GPU forms of the online stage.
 
-Polar factors of different matrices are independent, so the only exchange
-is moving results: whole matrices are assigned to ranks by longest
-processing time first on the algorithmic flops T (3 s^2 L + s^3), each rank
-runs one grouped call on the matrices it owns, and one all-gather of the
-flattened results gives every rank every factor (NCCL on GPUs; gloo works
-for host tensors).
+polar_sharded: one model's Muon matrices over ranks. Polar factors of
+different matrices are independent, so the only exchange is moving results:
+whole matrices are assigned to ranks by longest processing time first on the
+algorithmic flops T (3 s^2 L + s^3), each rank runs one grouped call on the
+matrices it owns, and one all-gather of the flattened results gives every
+rank every factor (NCCL on GPUs; gloo works for host tensors).
+
+polar_split_long: one matrix cut along its long side over ranks. The squared
+Frobenius norm and the Gram A = X X^T = sum_r X_r X_r^T are sums over the
+ranks' blocks, B = b A + c A^2 is the same everywhere and X_r <- a X_r + B X_r
+is local, so the exchange is one all-reduce of a scalar and one all-reduce
+of the s x s FP32 Gram per polynomial step (Alg. 1 online stage, A on the
+short side).
 """
 from __future__ import annotations
 
@@ -74,3 +81,32 @@ def polar_sharded(Xs: Sequence, table, dtype: str = "bf16", group=None,
             x.copy_(recv[o][pos[o]:pos[o] + x.numel()].view_as(x))
         pos[o] += x.numel()
     return Xs
+
+
+def polar_split_long(X, table, short_is_rows: bool, dtype: str = "bf16", group=None, ops=None):
+    """In place on this rank's block X of a matrix split along its long side.
+
+    ``ops`` overrides the rank-local computation (default: the library's
+    pe_split_* through paper_2505_16932_gb300.Split); it must provide
+    sumsq(), set_norm(total), gram(t, A), step(t, A) and close(), with A an
+    s x s tensor on X's device."""
+    import torch
+    import torch.distributed as dist
+
+    if ops is None:
+        from . import Split
+        ops = Split(X, short_is_rows, table, dtype)
+    s = X.shape[0] if short_is_rows else X.shape[1]
+    T = len(table)
+    try:
+        tot = torch.tensor([ops.sumsq()], dtype=torch.float64, device=X.device)
+        dist.all_reduce(tot, group=group)
+        ops.set_norm(float(tot.item()))
+        A = torch.empty((s, s), dtype=torch.float32 if X.is_cuda else torch.float64, device=X.device)
+        for t in range(T):
+            ops.gram(t, A)
+            dist.all_reduce(A, group=group)
+            ops.step(t, A)
+    finally:
+        ops.close()
+    return X

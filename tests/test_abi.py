@@ -98,3 +98,25 @@ def test_polar_argument_errors_without_gpu(L):
     ms = (ctypes.c_int64 * 1)(4)
     assert L.pe_polar_batched(ptrs, ms, ms, 1, tp, 5, pe.PE_BF16, None) == pe.PE_EINVAL
     assert L.pe_polar_batched(ptrs, ms, ms, 0, tp, 5, pe.PE_BF16, None) == pe.PE_EINVAL
+
+
+def test_split_argument_errors_without_gpu(L):
+    """pe_split_* validate their arguments before any CUDA call."""
+    tab = np.ones((5, 3))
+    P = ctypes.POINTER(ctypes.c_double)
+    tp = tab.ctypes.data_as(P)
+    fake = ctypes.c_void_p(0x10000)
+    h = ctypes.c_void_p()
+    assert L.pe_split_open(None, 4, 8, 1, tp, 5, pe.PE_BF16, None, ctypes.byref(h)) == pe.PE_EINVAL
+    assert L.pe_split_open(fake, 4, 8, 1, tp, 5, pe.PE_BF16X3, None, ctypes.byref(h)) == pe.PE_EUNSUPPORTED
+    assert L.pe_split_open(fake, 4, 8, 1, tp, 5, 7, None, ctypes.byref(h)) == pe.PE_EINVAL
+    assert L.pe_split_open(fake, 0, 8, 1, tp, 5, pe.PE_BF16, None, ctypes.byref(h)) == pe.PE_EINVAL
+    assert L.pe_split_open(fake, 4, 8, 1, tp, 0, pe.PE_BF16, None, ctypes.byref(h)) == pe.PE_EINVAL
+    assert L.pe_split_open(fake, 4, 8, 1, tp, 5, pe.PE_BF16, None, None) == pe.PE_EINVAL
+    assert h.value is None
+    d = ctypes.c_double()
+    assert L.pe_split_sumsq(None, ctypes.byref(d)) == pe.PE_EINVAL
+    assert L.pe_split_set_norm(None, 1.0) == pe.PE_EINVAL
+    assert L.pe_split_gram(None, 0, fake, 4) == pe.PE_EINVAL
+    assert L.pe_split_step(None, 0, fake, 4) == pe.PE_EINVAL
+    assert L.pe_split_close(None) == pe.PE_EINVAL

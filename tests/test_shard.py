@@ -87,3 +87,90 @@ def test_sharded_gloo_two_ranks(mode):
         assert list(out) == [1, 1]
     else:
         assert out[0] == 2          # the survivor's collective failed, it did not hang
+
+
+# ------------------------------------------------------ long-side split
+
+class _NumpySplitOps:
+    """Rank-local steps of the long-side split in FP64 (test stand-in for the
+    library's pe_split_*): X_r is the rank's block in the short-side layout."""
+
+    def __init__(self, X, short_is_rows, table):
+        self.X = X                                   # torch float64 block, written at the end
+        self.short_is_rows = short_is_rows
+        self.Xr = X.numpy().copy() if short_is_rows else X.numpy().T.copy()
+        self.table = table
+
+    def sumsq(self):
+        return float(np.sum(self.Xr * self.Xr))
+
+    def set_norm(self, total):
+        self.Xr = self.Xr / (1.01 * np.sqrt(total) + 1e-7)
+
+    def gram(self, t, A):
+        A.copy_(torch.from_numpy(self.Xr @ self.Xr.T))
+
+    def step(self, t, A):
+        a, b, c = self.table[t]
+        An = A.numpy()
+        self.Xr = a * self.Xr + (b * An + c * (An @ An)) @ self.Xr
+
+    def close(self):
+        self.X.copy_(torch.from_numpy(self.Xr if self.short_is_rows else self.Xr.T))
+
+
+def _split_worker(rank, world, port, mode, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=8))
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import oracle as O
+    table, _ = O.optimal_composition(1e-2, 5, safety=1.01)
+    ok = True
+    try:
+        for short_is_rows, (m, n) in ((True, (24, 70)), (False, (64, 20))):
+            G = np.random.default_rng(11).standard_normal((m, n))
+            L = n if short_is_rows else m
+            cuts = np.linspace(0, L, world + 1).astype(int)      # local extents may be < s
+            lo, hi = cuts[rank], cuts[rank + 1]
+            Gr = G[:, lo:hi] if short_is_rows else G[lo:hi, :]
+            X = torch.from_numpy(Gr.copy())
+            if mode == "dead" and rank == 1:
+                return   # leaves before the first exchange
+            shard.polar_split_long(X, table, short_is_rows, group=None, ops=_NumpySplitOps(X, short_is_rows, table))
+            ref = O.polar_express(G, table)
+            refr = ref[:, lo:hi] if short_is_rows else ref[lo:hi, :]
+            ok = ok and np.allclose(X.numpy(), refr, atol=1e-12, rtol=0)
+        out[rank] = 1 if ok else 0
+    except RuntimeError:
+        out[rank] = 2
+    finally:
+        try:
+            dist.destroy_process_group()
+        except Exception:
+            pass
+
+
+@pytest.mark.parametrize("world,mode", [(2, "ok"), (3, "ok"), (2, "dead")])
+def test_split_long_side_gloo(world, mode):
+    """Long-side split over gloo ranks: one all-reduce of the squared norm and
+    one of the Gram per step reproduce the FP64 iteration of the whole matrix
+    on every rank's block, in both orientations, with local extents smaller
+    than the short side; a rank that leaves makes the others' collective fail
+    within the timeout instead of hanging."""
+    ctx = mp.get_context("spawn")
+    out = ctx.Array("i", [-1] * world)
+    port = _free_port()
+    procs = [ctx.Process(target=_split_worker, args=(r, world, port, mode, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(60)
+        if p.is_alive():
+            p.kill()
+            pytest.fail("rank did not finish")
+    if mode == "ok":
+        assert list(out) == [1] * world
+    else:
+        assert out[0] == 2
