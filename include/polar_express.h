@@ -286,6 +286,30 @@ int pe_debug_set(int key, int64_t value);
  */
 int pe_polar_noalloc(void* X, int64_t m, int64_t n, const double* table, int T, void* stream);
 
+/* --------------------------------------------------- fused Muon step
+ *
+ * The Muon update (Sec. 2.1): M <- beta M + (1 - beta) G,
+ * W <- W - lr polar(M), with polar(M) by the Polar Express iteration of
+ * pe_polar_batched. The momentum update is fused into the normalisation
+ * kernel (it reads G and M once and writes M once) and the weight update into
+ * the last polynomial step's epilogue (a TMA reduce-add of -lr X_T into W where
+ * W's layout admits TMA, else a read-modify-write); polar(M) itself is never
+ * stored.
+ *   W, G, M  arrays of count device pointers to FP32 m[i] x n[i] row-major
+ *            contiguous matrices: W in/out, G in, M in/out (M_0 = 0 is the
+ *            caller's initialisation).
+ *   beta     momentum coefficient in [0, 1] (paper default 0.9); the new M is
+ *            fma(beta, M, (1 - beta) G) in FP32 with 1 - beta rounded to FP32.
+ *   lr       learning rate; W(i, j) becomes W(i, j) + (-lr X_T(i, j)), the
+ *            product and the sum each rounded to FP32.
+ *   table, T, dtype, flags, stream  as for pe_polar_batched_ex (fixed
+ *            normalisation constants 1.01 and 1e-7).
+ * A plan is cached per (pointers, shapes, T, dtype, table, beta, lr); the
+ * first call tunes it without changing M or W. Errors: as pe_polar_batched.
+ */
+int pe_muon_batched(void* const* W, void* const* G, void* const* M, const int64_t* m, const int64_t* n, int count,
+                    double beta, double lr, const double* table, int T, int dtype, unsigned flags, void* stream);
+
 /* ------------------------------------------------ long-side split (ranks)
  *
  * One matrix too large for one GPU, cut along its long side over R ranks

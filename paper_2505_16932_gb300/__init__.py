@@ -80,6 +80,8 @@ def lib() -> ctypes.CDLL:
         "pe_debug_set": (c_i, [c_i, c_i64]),
         "pe_trace_enable": (c_i, [c_i]),
         "pe_trace_read": (c_i, [P_i64, P_d, c_i]),
+        "pe_muon_batched": (c_i, [ctypes.POINTER(c_p), ctypes.POINTER(c_p), ctypes.POINTER(c_p), P_i64, P_i64, c_i,
+                                  c_d, c_d, P_d, c_i, c_i, c_u, c_p]),
         "pe_split_open": (c_i, [c_p, c_i64, c_i64, c_i, P_d, c_i, c_i, c_p, ctypes.POINTER(c_p)]),
         "pe_split_sumsq": (c_i, [c_p, P_d]),
         "pe_split_set_norm": (c_i, [c_p, c_d]),
@@ -199,6 +201,31 @@ def pe_polar_batched(Xs: Sequence, table, dtype: str = "bf16", stream=None, flag
                                      ctypes.c_void_p(_stream_handle(stream)))
     _check(code)
     return Xs
+
+
+def pe_muon_batched(Ws: Sequence, Gs: Sequence, Ms: Sequence, beta: float, lr: float, table,
+                    dtype: str = "bf16", stream=None, flags: int = 0):
+    """Fused Muon update on lists of contiguous float32 CUDA tensors of equal
+    shapes per index: M <- beta M + (1 - beta) G, W <- W - lr polar(M)."""
+    n = len(Ws)
+    if n == 0:
+        return Ws
+    if len(Gs) != n or len(Ms) != n:
+        raise PolarExpressError(PE_EINVAL, "W, G and M lists must have the same length")
+    for W, G, M in zip(Ws, Gs, Ms):
+        for t in (W, G, M):
+            _check_tensor(t)
+            if not t.is_contiguous() or _io_of(t) != PE_IO_FP32:
+                raise PolarExpressError(PE_EINVAL, "W, G, M must be contiguous float32 tensors")
+        if not (W.shape == G.shape == M.shape):
+            raise PolarExpressError(PE_EINVAL, "W, G and M must have the same shape")
+    arr = lambda ts: (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
+    ms = (ctypes.c_int64 * n)(*[t.shape[0] for t in Gs])
+    ns = (ctypes.c_int64 * n)(*[t.shape[1] for t in Gs])
+    tab = _table(table)
+    _check(lib().pe_muon_batched(arr(Ws), arr(Gs), arr(Ms), ms, ns, n, float(beta), float(lr), _dptr(tab),
+                                 tab.shape[0], DTYPES[dtype], int(flags), ctypes.c_void_p(_stream_handle(stream))))
+    return Ws
 
 
 def pe_sync_status(stream=None) -> int:

@@ -131,10 +131,13 @@ struct PlanKey {
     std::vector<uintptr_t> ptrs;
     std::vector<int64_t> dims;   // m, n, ld per matrix
     std::vector<float> coef;     // 3*T
+    // fused Muon step: momentum and weight buffers per matrix (empty otherwise)
+    std::vector<uintptr_t> mom, w;
+    float beta = 0.f, lr = 0.f;
     bool operator==(const PlanKey& o) const {
         return dev == o.dev && dtype == o.dtype && T == o.T && io == o.io && count == o.count &&
                flags == o.flags && scale == o.scale && eps == o.eps && ptrs == o.ptrs &&
-               dims == o.dims && coef == o.coef;
+               dims == o.dims && coef == o.coef && mom == o.mom && w == o.w && beta == o.beta && lr == o.lr;
     }
 };
 
@@ -200,6 +203,12 @@ int build_plan(const PlanKey& key, Plan** out) {
         memset(&M, 0, sizeof(M));
         const int64_t m = key.dims[3 * i], n = key.dims[3 * i + 1], ld = key.dims[3 * i + 2];
         M.user = reinterpret_cast<void*>(key.ptrs[i]);
+        if (!key.w.empty()) {
+            M.mom = reinterpret_cast<float*>(key.mom[i]);
+            M.w = reinterpret_cast<float*>(key.w[i]);
+            M.beta = key.beta;
+            M.lr = key.lr;
+        }
         M.ld = ld;
         M.m = (int32_t)m;
         M.n = (int32_t)n;
@@ -361,6 +370,8 @@ int enqueue(Plan* P, cudaStream_t st, bool tuning = false) {
     int outputs = kPrepF32;                                               // FP32
     if (k.dtype == PE_BF16) outputs = kPrepCode;                          // hi + code (compact master)
     if (k.dtype == PE_BF16X3) outputs = kPrepF32 | kPrepBF16 | kPrepBF16Lo;
+    if (!k.w.empty()) outputs |= kPrepMuon;                              // fused Muon step: momentum in prepare
+    if (tuning) outputs |= kPrepNoMom;                                    // a tuning run leaves M unchanged
     {
         TraceScope ts(1, st);
         PE_CU(launch_prepare(P->d_mats, k.count, P->d_prep, P->n_prep, P->d_partials, k.scale, k.eps, outputs,
@@ -546,7 +557,8 @@ int get_plan(const PlanKey& key, cudaStream_t st, Plan** out, bool* fresh) {
 }
 
 int run(void* const* X, const int64_t* m, const int64_t* n, const int64_t* ld, int count, int io,
-        const double* table, int T, int dtype, double scale, double eps, unsigned flags, void* stream) {
+        const double* table, int T, int dtype, double scale, double eps, unsigned flags, void* stream,
+        void* const* Mom = nullptr, void* const* W = nullptr, double beta = 0.0, double lr = 0.0) {
     if (!X || !m || !n) return fail(PE_EINVAL, "NULL argument");
     if (count < 1 || count > kMaxMatrices) return fail(PE_EINVAL, "count must be in 1..4096");
     if (!table) return fail(PE_EINVAL, "table is NULL");
@@ -583,6 +595,23 @@ int run(void* const* X, const int64_t* m, const int64_t* n, const int64_t* ld, i
     for (int i = 0; i < 3 * T; ++i) {
         if (!std::isfinite(table[i])) return fail(PE_EINVAL, "non-finite coefficient in table");
         key.coef[i] = (float)table[i];
+    }
+    if (W) {
+        if (!Mom) return fail(PE_EINVAL, "momentum pointer array is NULL");
+        if (io != PE_IO_FP32) return fail(PE_EINVAL, "the fused Muon step takes FP32 matrices");
+        if (!(std::isfinite(beta) && beta >= 0 && beta <= 1)) return fail(PE_EINVAL, "beta must be in [0, 1]");
+        if (!std::isfinite(lr)) return fail(PE_EINVAL, "lr must be finite");
+        key.mom.resize(count);
+        key.w.resize(count);
+        for (int i = 0; i < count; ++i) {
+            if (!Mom[i] || !W[i]) return fail(PE_EINVAL, "momentum or weight pointer " + std::to_string(i) + " is NULL");
+            if (reinterpret_cast<uintptr_t>(Mom[i]) % 4 || reinterpret_cast<uintptr_t>(W[i]) % 4)
+                return fail(PE_EINVAL, "misaligned momentum or weight pointer");
+            key.mom[i] = reinterpret_cast<uintptr_t>(Mom[i]);
+            key.w[i] = reinterpret_cast<uintptr_t>(W[i]);
+        }
+        key.beta = (float)beta;
+        key.lr = (float)lr;
     }
     std::lock_guard<std::mutex> lk(g_mu);
     PE_CU(cudaGetDevice(&key.dev));
@@ -923,6 +952,12 @@ int pe_split_close(pe_split_t h) {
     delete h;
     if (e != cudaSuccess) return pe::cuda_fail(e, "cudaStreamSynchronize");
     return PE_OK;
+}
+
+int pe_muon_batched(void* const* W, void* const* G, void* const* M, const int64_t* m, const int64_t* n, int count,
+                    double beta, double lr, const double* table, int T, int dtype, unsigned flags, void* stream) {
+    if (!W || !G || !M) return pe::fail(PE_EINVAL, "NULL pointer array");
+    return pe::run(G, m, n, nullptr, count, PE_IO_FP32, table, T, dtype, 1.01, 1e-7, flags, stream, M, W, beta, lr);
 }
 
 int pe_debug_set(int key, int64_t value) {

@@ -59,6 +59,12 @@ struct DevMat {
     float* bfp;          // FP32 B (FP32 path)
     bf16* bh;            // BF16 B = bA + cA^2 (hi)
     bf16* bl;            // BF16 B lo (BF16x3)
+    // fused Muon step (pe_muon_batched): `user` is the gradient G, `mom` the
+    // momentum M <- beta M + (1 - beta) G (the iteration's input) and `w` the
+    // weights W <- W - lr polar(M); all FP32 with the caller's shape and ld.
+    float* mom;
+    float* w;
+    float beta, lr;
 };
 
 struct TileTask { int32_t mat, tm, tn, kind; };  // kind: 0 Gram, 1 A^2, 2 update
@@ -66,7 +72,19 @@ struct TileTask { int32_t mat, tm, tn, kind; };  // kind: 0 Gram, 1 A^2, 2 updat
 enum TileKind { kGram = 0, kSquare = 1, kApply = 2 };
 
 // Which canonical buffers the prepare kernel fills.
-enum PrepOut { kPrepF32 = 1, kPrepBF16 = 2, kPrepBF16Lo = 4, kPrepCode = 8 };
+enum PrepOut { kPrepF32 = 1, kPrepBF16 = 2, kPrepBF16Lo = 4, kPrepCode = 8,
+               kPrepNoMom = 16,     // fused Muon: compute the momentum but leave M unchanged (tuning runs)
+               kPrepMuon = 32 };    // fused Muon: the kernel instantiation with the momentum update
+
+// Final store of element (i, l) of the canonical result X_T: into the
+// caller's matrix, or for a fused Muon step W(i, l) <- W(i, l) - lr X_T(i, l).
+__device__ __forceinline__ void out_user(const DevMat& M, int i, int l, float v) {
+    if (i >= M.s || l >= M.L) return;
+    const int64_t idx = M.trans ? (int64_t)l * M.ld + i : (int64_t)i * M.ld + l;
+    if (M.w) M.w[idx] = __fadd_rn(M.w[idx], __fmul_rn(-M.lr, v));   // the rounding of a TMA reduce-add
+    else if (M.io == PE_IO_BF16) reinterpret_cast<bf16*>(M.user)[idx] = __float2bfloat16_rn(v);
+    else reinterpret_cast<float*>(M.user)[idx] = v;
+}
 
 // Compact master of X on the BF16 path: X is kept as hi = BF16 (the MMA
 // operand) and an 8-bit code of the next 8 mantissa bits, i.e. x rounded to a

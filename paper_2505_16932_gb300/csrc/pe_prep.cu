@@ -49,6 +49,40 @@ __device__ __forceinline__ float4 load4(const DevMat& M, bool vec, int rows, int
     return r;
 }
 
+// Fused Muon step: M <- beta M + (1 - beta) G at the four inputs just read
+// (same indices in M), stored back unless `store` is off; returns the new M,
+// the value the iteration runs on.
+__device__ __forceinline__ float4 momentum4(const DevMat& M, bool vec, int rows, int cols, int row, int col, float4 g,
+                                            bool store) {
+    if (row >= rows) return g;
+    const float omb = 1.f - M.beta;
+    const int64_t base = (int64_t)row * M.ld + col;
+    float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (vec && col + 3 < cols) {
+        m = __ldcs(reinterpret_cast<const float4*>(M.mom + base));
+    } else {
+        if (col + 0 < cols) m.x = M.mom[base + 0];
+        if (col + 1 < cols) m.y = M.mom[base + 1];
+        if (col + 2 < cols) m.z = M.mom[base + 2];
+        if (col + 3 < cols) m.w = M.mom[base + 3];
+    }
+    const float4 r = make_float4(fmaf(M.beta, m.x, __fmul_rn(omb, g.x)), fmaf(M.beta, m.y, __fmul_rn(omb, g.y)),
+                                 fmaf(M.beta, m.z, __fmul_rn(omb, g.z)), fmaf(M.beta, m.w, __fmul_rn(omb, g.w)));
+    if (store) {
+        if (vec && col + 3 < cols) {
+            *reinterpret_cast<float4*>(M.mom + base) = r;
+        } else {
+            if (col + 0 < cols) M.mom[base + 0] = r.x;
+            if (col + 1 < cols) M.mom[base + 1] = r.y;
+            if (col + 2 < cols) M.mom[base + 2] = r.z;
+            if (col + 3 < cols) M.mom[base + 3] = r.w;
+        }
+    }
+    // padding stays zero
+    return make_float4(col + 0 < cols ? r.x : 0.f, col + 1 < cols ? r.y : 0.f, col + 2 < cols ? r.z : 0.f,
+                       col + 3 < cols ? r.w : 0.f);
+}
+
 __device__ __forceinline__ uint32_t pack2(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
@@ -81,6 +115,7 @@ __device__ __forceinline__ void put4(const DevMat& M, int outputs, int64_t o, fl
     }
 }
 
+template <bool MUON>
 __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__ mats, int nmats,
                                                       const TileTask* __restrict__ tiles,
                                                       double* __restrict__ partials, float scale, float eps,
@@ -98,7 +133,9 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
     const int i0 = tk.tm * kPrepRows, l0 = tk.tn * kPrepCols;
     const int tid = threadIdx.x;
     const int esz = (M.io == PE_IO_BF16) ? 2 : 4;
-    const bool vec = (reinterpret_cast<uintptr_t>(M.user) % (4 * esz) == 0) && (M.ld % 4 == 0);
+    const bool vec = (reinterpret_cast<uintptr_t>(M.user) % (4 * esz) == 0) && (M.ld % 4 == 0) &&
+                     (!MUON || reinterpret_cast<uintptr_t>(M.mom) % 16 == 0);
+    const bool mom_store = !(outputs & kPrepNoMom);
     float ss = 0.f;
     // all sixteen loads of a thread are issued before any store (the
     // compiler cannot move loads of G across stores that may alias it)
@@ -110,6 +147,10 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
 #pragma unroll
         for (int p = 0; p < 16; ++p)
             ld[p] = on ? load4(M, vec, M.s, M.L, i0 + r0 + 4 * p, l0 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (MUON && on) {
+#pragma unroll
+            for (int p = 0; p < 16; ++p) ld[p] = momentum4(M, vec, M.s, M.L, i0 + r0 + 4 * p, l0 + c, ld[p], mom_store);
+        }
         if (on) {
 #pragma unroll
             for (int p = 0; p < 16; ++p) {
@@ -126,6 +167,13 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
         for (int p = 0; p < 16; ++p) {
             const int l = l0 + rr + 16 * p;   // sub-tile p / 4, row rr + 16 (p % 4)
             ld[p] = (l < M.Lp) ? load4(M, vec, M.L, M.s, l, i0 + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (MUON) {
+#pragma unroll
+            for (int p = 0; p < 16; ++p) {
+                const int l = l0 + rr + 16 * p;
+                if (l < M.Lp) ld[p] = momentum4(M, vec, M.L, M.s, l, i0 + c4, ld[p], mom_store);
+            }
         }
 #pragma unroll
         for (int k = 0; k < kPrepCols / 64; ++k) {
@@ -213,8 +261,12 @@ cudaError_t launch_split_load_a(const float* A, int64_t lda, int s, int sp, bf16
 cudaError_t launch_prepare(const DevMat* mats, int nmats, const TileTask* tiles, int ntiles, double* partials,
                            float scale, float eps, int outputs, float* nscale, int* status, int* counters,
                            int ncounters, unsigned* ticket, cudaStream_t st) {
-    prepare_kernel<<<ntiles, 256, 0, st>>>(mats, nmats, tiles, partials, scale, eps, outputs, nscale, status,
-                                           counters, ncounters, ticket);
+    if (outputs & kPrepMuon)
+        prepare_kernel<true><<<ntiles, 256, 0, st>>>(mats, nmats, tiles, partials, scale, eps, outputs, nscale,
+                                                     status, counters, ncounters, ticket);
+    else
+        prepare_kernel<false><<<ntiles, 256, 0, st>>>(mats, nmats, tiles, partials, scale, eps, outputs, nscale,
+                                                      status, counters, ncounters, ticket);
     return cudaGetLastError();
 }
 

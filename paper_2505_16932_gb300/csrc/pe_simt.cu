@@ -70,13 +70,6 @@ __device__ __forceinline__ void store_tiles(float (*As)[BM], float (*Bs)[BN], in
     }
 }
 
-__device__ __forceinline__ void store_out(const DevMat& M, int i, int l, float v) {
-    if (i >= M.s || l >= M.L) return;
-    const int64_t idx = M.trans ? (int64_t)l * M.ld + i : (int64_t)i * M.ld + l;
-    if (M.io == PE_IO_BF16) reinterpret_cast<bf16*>(M.user)[idx] = __float2bfloat16_rn(v);
-    else reinterpret_cast<float*>(M.user)[idx] = v;
-}
-
 template <int kKind>
 __global__ void __launch_bounds__(256) simt_phase_kernel(const DevMat* __restrict__ mats,
                                                          const TileTask* __restrict__ tiles,
@@ -170,7 +163,7 @@ __global__ void __launch_bounds__(256) simt_phase_kernel(const DevMat* __restric
                 for (int j = 0; j < 4; ++j) v[j] = s0 * fmaf(ca, xv[j], v[j]);
                 if (last) {
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) store_out(M, r, c + j, v[j]);
+                    for (int j = 0; j < 4; ++j) out_user(M, r, c + j, v[j]);
                 } else {
                     *reinterpret_cast<float4*>(xd + (int64_t)r * M.Lp + c) = make_float4(v[0], v[1], v[2], v[3]);
                 }

@@ -207,6 +207,14 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t sr
                  : "memory");
 }
 
+// element-wise add of the box into global memory (f32, round to nearest)
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
+    asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
@@ -394,12 +402,6 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-__device__ __forceinline__ void store_user(const DevMat& M, int i, int l, float v) {
-    if (i >= M.s || l >= M.L) return;
-    const int64_t idx = M.trans ? (int64_t)l * M.ld + i : (int64_t)i * M.ld + l;
-    if (M.io == PE_IO_BF16) reinterpret_cast<bf16*>(M.user)[idx] = __float2bfloat16_rn(v);
-    else reinterpret_cast<float*>(M.user)[idx] = v;
-}
 
 // Swizzled 32 x 32 staging boxes. FP32 rows are 128 bytes (128-byte swizzle:
 // 16-byte chunk c of row r lives at chunk c ^ (r & 7)); BF16 rows are 64
@@ -553,7 +555,7 @@ __device__ __forceinline__ void chunk_hl(const Geo& g, const DevMat& M, const St
         for (int j = 0; j < 32; ++j) v[j] = s0 * fmaf(A.a, pre[j], v[j]);
         if (A.last) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) store_user(M, gi, col0 + j, v[j]);
+            for (int j = 0; j < 32; ++j) out_user(M, gi, col0 + j, v[j]);
             return;
         }
         float* xrow = M.xf + (int64_t)gi * M.Lp + col0;
@@ -1050,6 +1052,10 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                         stage_x_row(s_out, s_out + 2048, lane, v);
                     } else if (g.kind == kApply) {
                         if (M.out_tma) {
+                            if (M.w) {   // fused Muon step: the box holds -lr X_T, reduce-added into W
+#pragma unroll
+                                for (int j = 0; j < 32; ++j) v[j] = __fmul_rn(-M.lr, v[j]);
+                            }
                             if (M.io == PE_IO_BF16) {
                                 if (M.trans) stage_bf16_col(s_out, lane, v); else stage_bf16_row(s_out, lane, v);
                             } else {
@@ -1057,7 +1063,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                             }
                         } else {
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) store_user(M, gi, col0 + j, v[j]);
+                            for (int j = 0; j < 32; ++j) out_user(M, gi, col0 + j, v[j]);
                         }
                     } else if (cls == kChunkDiag) {
                         stage_bf16_sym(s_out, lane, v);
@@ -1077,8 +1083,9 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                             tma_store_2d(mp + (A.cur ? kMapEXH0 : kMapEXH1), smem_u32(s_out), col0, gi0);
                             tma_store_2d(mp + kMapEXQ, smem_u32(s_out + 2048), col0, gi0);
                         } else if (g.kind == kApply) {
-                            if (M.trans) tma_store_2d(mp + kMapEOut, smem_u32(s_out), gi0, col0);
-                            else tma_store_2d(mp + kMapEOut, smem_u32(s_out), col0, gi0);
+                            const int ox = M.trans ? gi0 : col0, oy = M.trans ? col0 : gi0;
+                            if (M.w) tma_reduce_add_2d(mp + kMapEOut, smem_u32(s_out), ox, oy);
+                            else tma_store_2d(mp + kMapEOut, smem_u32(s_out), ox, oy);
                         } else {
                             const CUtensorMap* hm = mp + ((g.kind == kGram && !A.cubic) ? kMapEAH : kMapEBH);
                             tma_store_2d(hm, smem_u32(s_out), col0, gi0);
@@ -1485,8 +1492,9 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
         // a 16-byte multiple pitch
         const int esz = (M.io == PE_IO_BF16) ? 2 : 4;
         M.out_tma = 0;
-        if (P->nsplit == 1 && reinterpret_cast<uintptr_t>(M.user) % 16 == 0 && (M.ld * esz) % 16 == 0) {
-            M.out_tma = make_map(enc, mp + kMapEOut, M.user, M.m, M.n, M.ld * esz, 32, 32, esz == 4 ? F32 : BF,
+        void* out = M.w ? (void*)M.w : M.user;   // fused Muon step: the box is reduce-added into W
+        if (P->nsplit == 1 && reinterpret_cast<uintptr_t>(out) % 16 == 0 && (M.ld * esz) % 16 == 0) {
+            M.out_tma = make_map(enc, mp + kMapEOut, out, M.m, M.n, M.ld * esz, 32, 32, esz == 4 ? F32 : BF,
                                  esz == 4 ? S128 : S64)
                             ? 1
                             : 0;
