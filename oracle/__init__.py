@@ -36,6 +36,8 @@ from .minimax import (  # noqa: F401
 )
 from .iteration import (  # noqa: F401
     normalise,
+    fast_rectangular,
+    fast_rectangular_spectral,
     polar_express,
     polar_express_spectral,
     compose_scalar,

@@ -12,6 +12,10 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 * ``polar_express_spectral``: the same map written through the SVD,
   U p(x) V^T with x the normalised singular values (Sec. 2 definition of p(M)
   and App. C), for inputs whose factors are known.
+* ``fast_rectangular``: Alg. 4 (the appendix on fast polynomial iteration for
+  rectangular matrices): Y = X X^T, Q_t = Q_{t-1} h_t(Q^T Y Q), X_T = Q_T X,
+  restarted every few steps, with the shift Y + 1e-3 I in the first block;
+  ``fast_rectangular_spectral`` is the same map on the singular values.
 * ``polar_svd``: polar(G) = U V^T (Eq. matrixsign).
 * error metrics: ||X - polar(G)||_F / sqrt(min(m, n)), max_i |sigma_i(X) - 1|,
   their restriction to singular directions with sigma_i(G) >= gamma sigma_max
@@ -55,6 +59,68 @@ def polar_express(G: np.ndarray, table: Iterable[Sequence[float]],
     out = X.T if transposed else X
     out = np.ascontiguousarray(out)
     return (out, steps) if return_steps else out
+
+
+FAST_SHIFT = 1e-3      # stabiliser of the first application (appendix on rectangular matrices)
+FAST_EPS = 1e-3        # normalisation offset used with it
+
+
+def fast_rectangular(G: np.ndarray, table: Iterable[Sequence[float]], restart: int = 3,
+                     shift: float = FAST_SHIFT, scale: float = NORM_SCALE, eps: float = FAST_EPS,
+                     return_blocks: bool = False):
+    """Alg. 4 (fast polynomial iteration for rectangular matrices) in FP64, on
+    the short side: X s x L, p_t(X) = h_t(X X^T) X with h_t(y) = a + b y + c y^2.
+
+    The steps are taken in blocks of ``restart`` (the restarting strategy of
+    the same appendix; restart = 1 is the baseline iteration). For a block:
+    Y = X X^T (+ shift I in the first block only), Q = I, then per step
+    R = Q^T Y Q and Q = Q h(R); finally X = Q X. The normalisation divides by
+    scale ||G||_F + eps (the appendix uses ||X||_F + 1e-3 with the shift)."""
+    X, transposed = normalise(G, scale, eps)
+    s = X.shape[0]
+    rows = [tuple(r) for r in table]
+    blocks = []
+    t = 0
+    first = True
+    while t < len(rows):
+        Y = X @ X.T
+        if first and shift:
+            Y = Y + shift * np.eye(s)
+        Q = np.eye(s)
+        for (a, b, c) in rows[t:t + restart]:
+            R = Q.T @ Y @ Q
+            H = a * np.eye(s) + b * R + c * (R @ R)
+            Q = Q @ H
+        X = Q @ X
+        t += restart
+        first = False
+        if return_blocks:
+            blocks.append(X.T.copy() if transposed else X.copy())
+    out = np.ascontiguousarray(X.T if transposed else X)
+    return (out, blocks) if return_blocks else out
+
+
+def fast_rectangular_spectral(U: np.ndarray, s: np.ndarray, V: np.ndarray, table, restart: int = 3,
+                              shift: float = FAST_SHIFT, scale: float = NORM_SCALE, eps: float = FAST_EPS):
+    """The map of ``fast_rectangular`` on G = U diag(s) V^T written through the
+    singular values: with x = s / (scale ||s|| + eps), every block takes
+    y = x^2 (+ shift in the first block), q = 1, and per step
+    q <- q h(y q^2); then x <- x q. (Y, Q, R are polynomials of one symmetric
+    matrix, so the recursion acts on each eigenvalue separately.)"""
+    x = np.asarray(s, dtype=np.float64) / (scale * math.sqrt(float(np.sum(np.asarray(s, np.float64) ** 2))) + eps)
+    rows = [tuple(r) for r in table]
+    t = 0
+    first = True
+    while t < len(rows):
+        y = x * x + (shift if first and shift else 0.0)
+        q = np.ones_like(x)
+        for (a, b, c) in rows[t:t + restart]:
+            r = y * q * q
+            q = q * (a + b * r + c * r * r)
+        x = x * q
+        t += restart
+        first = False
+    return (U * x) @ V.T
 
 
 def compose_scalar(x, table: Iterable[Sequence[float]]):

@@ -167,3 +167,69 @@ def test_restricted_errors():
     assert fro < 1e-13 and mx < 1e-13
     fro, mx = O.restricted_errors(0.9 * P, case.U, case.s, case.V)
     assert abs(mx - 0.1) < 1e-12
+
+
+# ----------------------------------------- Alg. 4 (fast rectangular iteration)
+
+@pytest.mark.parametrize("m,n", [(40, 170), (170, 40), (32, 32)])
+def test_fast_rectangular_restart_one_is_the_baseline(m, n):
+    """Restarting after every step is the baseline method (appendix on
+    rectangular matrices): same normalisation, no shift."""
+    G = np.random.default_rng(m * n).standard_normal((m, n))
+    tab, _ = O.optimal_composition(1e-3, 6, safety=1.01)
+    ref = O.polar_express(G, tab, scale=1.01, eps=1e-3)
+    got = O.fast_rectangular(G, tab, restart=1, shift=0.0)
+    assert np.max(np.abs(got - ref)) <= 1e-12
+
+
+@pytest.mark.parametrize("restart", [2, 3, 6])
+def test_fast_rectangular_without_shift_equals_the_baseline(restart):
+    """Without the shift, X_T = Q_T X_0 = (p_T o ... o p_1)(X_0) (the induction
+    of the appendix): any restart interval gives the baseline's result up to
+    FP64 rounding on a well-conditioned input."""
+    case = synth.random_svd_case(seed=7, m=48, n=200, lo=0.1)
+    tab, _ = O.optimal_composition(1e-1, 6, safety=1.01)
+    ref = O.polar_express(case.G, tab, scale=1.01, eps=1e-3)
+    got = O.fast_rectangular(case.G, tab, restart=restart, shift=0.0)
+    assert np.max(np.abs(got - ref)) <= 1e-10
+
+
+@pytest.mark.parametrize("restart,shift", [(3, 1e-3), (2, 1e-3), (6, 1e-2)])
+@pytest.mark.parametrize("m,n", [(40, 160), (160, 40)])
+def test_fast_rectangular_matches_its_spectral_form(restart, shift, m, n):
+    """Matrix recursion (Y, Q, R) against the scalar recursion on the
+    singular values, q <- q h(y q^2), with the shift only in the first block."""
+    case = synth.random_svd_case(seed=m + n + restart, m=m, n=n, lo=1e-3)
+    tab, _ = O.optimal_composition(1e-3, 6, safety=1.01)
+    got = O.fast_rectangular(case.G, tab, restart=restart, shift=shift)
+    ref = O.fast_rectangular_spectral(case.U, case.s, case.V, tab, restart=restart, shift=shift)
+    assert np.max(np.abs(got - ref)) <= 1e-10
+
+
+def test_fast_rectangular_shift_only_in_first_block():
+    """The shift changes the first block only: the later blocks are the plain
+    iteration applied to the first block's output."""
+    case = synth.random_svd_case(seed=3, m=30, n=120, lo=1e-2)
+    tab, _ = O.optimal_composition(1e-2, 6, safety=1.01)
+    full, blocks = O.fast_rectangular(case.G, tab, restart=3, return_blocks=True)
+    X3 = blocks[0]
+    # the remaining 3 steps without shift, on X3 as already normalised (scale 1, eps 0)
+    X = X3.copy()
+    for (a, b, c) in tab[3:]:
+        A = X @ X.T
+        X = a * X + (b * A + c * (A @ A)) @ X
+    assert np.max(np.abs(full - X)) <= 1e-10
+    # and the first block differs from the unshifted one
+    noshift = O.fast_rectangular(case.G, tab[:3], restart=3, shift=0.0)
+    assert np.max(np.abs(noshift - X3)) > 1e-4
+
+
+def test_fast_rectangular_still_converges_to_polar():
+    """With the shift the early output differs, yet the restarted iteration
+    still converges to polar(G) (the appendix's remark): 4 blocks of 3."""
+    case = synth.random_svd_case(seed=5, m=32, n=128, lo=1e-2)
+    tab, _ = O.optimal_composition(1e-2, 12, safety=1.01)
+    got = O.fast_rectangular(case.G, tab, restart=3)
+    P = (case.U @ case.V.T)
+    assert O.err_polar_fro(got, P) <= 1e-6
+    assert O.max_sigma_err(got) <= 1e-6
