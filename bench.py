@@ -49,6 +49,7 @@ L2_BYTES = 129 * 1024 * 1024
 WORKLOADS = {
     "gpt2_small": lambda: synth.gpt2_small(),
     "uneven_d1024": lambda: synth.uneven_d1024(),
+    "gpt2_heads": lambda: synth.gpt2_heads(),
     "large_dense": lambda: synth.large_dense(),
     "ill_conditioned": lambda: synth.ill_conditioned(),
     "plain_small": lambda: synth.plain_small(),

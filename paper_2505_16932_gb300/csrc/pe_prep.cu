@@ -144,9 +144,17 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
         // X[i][l] = G[i][l]; G is s x L. 64 threads per row, 4 rows per pass.
         const int c = (tid & 63) * 4, r0 = tid >> 6;
         const bool on = l0 + c < M.Lp;   // the last strip of a row may be 128 wide
+        // interior strip of an FP32 matrix: sixteen unconditional vector loads
+        const bool interior = vec && M.io != PE_IO_BF16 && i0 + kPrepRows <= M.s && l0 + kPrepCols <= M.L;
+        if (interior) {
+            const float* g = reinterpret_cast<const float*>(M.user) + (int64_t)(i0 + r0) * M.ld + l0 + c;
 #pragma unroll
-        for (int p = 0; p < 16; ++p)
-            ld[p] = on ? load4(M, vec, M.s, M.L, i0 + r0 + 4 * p, l0 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int p = 0; p < 16; ++p) ld[p] = __ldcs(reinterpret_cast<const float4*>(g + (int64_t)4 * p * M.ld));
+        } else {
+#pragma unroll
+            for (int p = 0; p < 16; ++p)
+                ld[p] = on ? load4(M, vec, M.s, M.L, i0 + r0 + 4 * p, l0 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         if (MUON && on) {
 #pragma unroll
             for (int p = 0; p < 16; ++p) ld[p] = momentum4(M, vec, M.s, M.L, i0 + r0 + 4 * p, l0 + c, ld[p], mom_store);
@@ -163,10 +171,17 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
         // X[i][l] = G[l][i]; G is L x s: read G rows l with i contiguous (16
         // threads per 64-float row segment), transpose 64 x 64 sub-tiles in smem
         const int rr = tid >> 4, c4 = (tid & 15) * 4;
+        const bool interior = vec && M.io != PE_IO_BF16 && l0 + kPrepCols <= M.L && i0 + kPrepRows <= M.s;
+        if (interior) {
+            const float* g = reinterpret_cast<const float*>(M.user) + (int64_t)(l0 + rr) * M.ld + i0 + c4;
 #pragma unroll
-        for (int p = 0; p < 16; ++p) {
-            const int l = l0 + rr + 16 * p;   // sub-tile p / 4, row rr + 16 (p % 4)
-            ld[p] = (l < M.Lp) ? load4(M, vec, M.L, M.s, l, i0 + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int p = 0; p < 16; ++p) ld[p] = __ldcs(reinterpret_cast<const float4*>(g + (int64_t)16 * p * M.ld));
+        } else {
+#pragma unroll
+            for (int p = 0; p < 16; ++p) {
+                const int l = l0 + rr + 16 * p;   // sub-tile p / 4, row rr + 16 (p % 4)
+                ld[p] = (l < M.Lp) ? load4(M, vec, M.L, M.s, l, i0 + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
         if (MUON) {
 #pragma unroll

@@ -150,6 +150,34 @@ def gpt2_small(layers: int = 12, d: int = 768, first_seed: int = 1) -> Workload:
                     f"{layers} layers x (d x 3d, d x d, d x 4d, 4d x d), d={d}")
 
 
+def gpt2_heads_shapes(layers: int = 12, d: int = 768, heads: int = 12) -> List[Tuple[int, int]]:
+    """Per-head splitting of the attention weights (appendix on rectangular
+    matrices, application to Muon): per layer the q, k and v blocks of the
+    d x 3d weight and the d x d projection each split into ``heads`` slices
+    of d x d/heads; the MLP matrices stay whole."""
+    out = []
+    for _ in range(layers):
+        out += [(d, d // heads)] * (4 * heads)
+        out += [(d, 4 * d), (4 * d, d)]
+    return out
+
+
+def gpt2_heads(layers: int = 12, d: int = 768, heads: int = 12, first_seed: int = 5000) -> Workload:
+    """GPT-2-small Muon step with per-head splitting: 576 slices of 768 x 64
+    plus the 24 MLP matrices; spectra as in gpt2_small (s_i = 1/i +
+    1e-3|N(0,1)|, unit Frobenius norm). Matrix j uses seed first_seed + j."""
+    mats, svds = [], []
+    for j, (m, n) in enumerate(gpt2_heads_shapes(layers, d, heads)):
+        rng = np.random.default_rng(first_seed + j)
+        sv_s = spectrum_gpt2(rng, min(m, n))
+        sv_s = sv_s / np.linalg.norm(sv_s)
+        sv = svd_matrix(rng, m, n, sv_s)
+        mats.append(sv.G)
+        svds.append(sv)
+    return Workload("gpt2_small_per_head", mats, svds, 1e-3, 5, "bf16",
+                    f"{layers} layers x ({4 * heads} heads of d x d/{heads}, d x 4d, 4d x d), d={d}")
+
+
 def uneven_d1024(layers: int = 24, d: int = 1024, extra: int = 16,
                  shape_seed: int = 2) -> Workload:
     """24 layers of a d=1024 model plus ``extra`` matrices with m, n drawn
