@@ -51,7 +51,7 @@ struct DevMat {
     float* xf2;          // FP32 ping-pong partner (FP32 path)
     bf16* xh[2];         // BF16 X (hi part), ping-pong
     bf16* xl[2];         // BF16 X lo part (BF16x3), ping-pong
-    int8_t* xq;          // BF16 path: code of the next 8 mantissa bits of X
+    int8_t* xq;          // BF16 path: byte of the next 8 mantissa bits of X
                          // below xh[cur] (see x_split), updated in place
     float* af;           // FP32 A = X X^T (FP32, BF16x3)
     bf16* ah;            // BF16 A (hi)
@@ -87,14 +87,14 @@ __device__ __forceinline__ void out_user(const DevMat& M, int i, int l, float v)
 }
 
 // Compact master of X on the BF16 path: X is kept as hi = BF16 (the MMA
-// operand) and an 8-bit code of the next 8 mantissa bits, i.e. x rounded to a
-// 16-bit mantissa, in 3 bytes instead of the 6 of an FP32 copy plus a BF16
+// operand) and one byte u holding the next 8 mantissa bits, i.e. x rounded to
+// a 16-bit mantissa, in 3 bytes instead of the 6 of an FP32 copy plus a BF16
 // operand. On the FP32 bit pattern b of x:
-//   t  = b + 0x8080,  hi = t >> 16    (BF16; rounds up from 0x7F80 of the low half)
-//   r  = b - (hi << 16) + 0x80,  code = r >> 8   (in [-128, 127]; byte 1 of r)
-//   x' = bits^-1((hi << 16) + (code << 8)),   |x' - x| <= 2^-16 |x|.
-// The rounding point 0x7F80 keeps b - (hi << 16) in [-0x8080, 0x7F80), so the
-// code never leaves a signed byte; zero maps to zero, signs never flip, and
+//   t  = b + 0x8080,   hi = t >> 16,   u = (t >> 8) & 0xFF
+//   x' = bits^-1((hi << 16) + (u << 8) - 0x8000),   |x' - x| <= 2^-16 |x|.
+// (hi rounds up from 0x7F80 of b's low half, not 0x8000, so that the signed
+// residual code u - 128 = (b - (hi << 16) + 0x80) >> 8 never leaves a byte;
+// u is that code in offset binary.) Zero maps to zero, signs never flip, and
 // everything is integer arithmetic on the bit pattern (exact, deterministic).
 
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
@@ -103,26 +103,22 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
     return d;
 }
 
-// t and r of x (see above)
-__device__ __forceinline__ void x_split(float x, uint32_t& t, uint32_t& r) {
-    const uint32_t b = __float_as_uint(x);
-    t = b + 0x8080u;
-    r = b - (t & 0xFFFF0000u) + 0x80u;
-}
+// t of x (see above): hi is its upper half, u its byte 1
+__device__ __forceinline__ uint32_t x_split(float x) { return __float_as_uint(x) + 0x8080u; }
 
 // hi of two elements from their t, the first in the low half
 __device__ __forceinline__ uint32_t hi_pair(uint32_t t0, uint32_t t1) { return prmt(t0, t1, 0x7632u); }
 
-// codes of four elements from their r (byte 1 of each), the first in the low byte
-__device__ __forceinline__ uint32_t code_quad(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
-    return prmt(prmt(r0, r1, 0x0051u), prmt(r2, r3, 0x0051u), 0x5410u);
+// u of four elements (byte 1 of each t), the first in the low byte
+__device__ __forceinline__ uint32_t code_quad(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3) {
+    return prmt(prmt(t0, t1, 0x0051u), prmt(t2, t3, 0x0051u), 0x5410u);
 }
 
-// x' from hi << 16 and byte k of a code word: prmt puts the byte in byte 1,
-// its sign in bytes 2-3 and zero in byte 0, i.e. code << 8
+// x' from hi << 16 and byte k of a code word: prmt moves the byte to byte 1
+// with zeros elsewhere, i.e. u << 8
 __device__ __forceinline__ float x_join(uint32_t hi32, uint32_t cw, int k) {
-    const uint32_t sel = ((8u | k) << 12) | ((8u | k) << 8) | ((uint32_t)k << 4) | 4u;
-    return __uint_as_float(hi32 + prmt(cw, 0u, sel));
+    const uint32_t sel = (4u << 12) | (4u << 8) | ((uint32_t)k << 4) | 4u;
+    return __uint_as_float(hi32 + prmt(cw, 0u, sel) - 0x8000u);
 }
 
 // ---- launchers (return cudaError_t of the launch) ----

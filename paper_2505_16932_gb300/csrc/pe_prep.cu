@@ -92,13 +92,9 @@ __device__ __forceinline__ void put4(const DevMat& M, int outputs, int64_t o, fl
     if (outputs & kPrepF32) *reinterpret_cast<float4*>(M.xf + o) = v;
     if (outputs & kPrepCode) {
         // BF16 path: hi and code of the compact master (x_split)
-        uint32_t t0, t1, t2, t3, r0, r1, r2, r3;
-        x_split(v.x, t0, r0);
-        x_split(v.y, t1, r1);
-        x_split(v.z, t2, r2);
-        x_split(v.w, t3, r3);
+        const uint32_t t0 = x_split(v.x), t1 = x_split(v.y), t2 = x_split(v.z), t3 = x_split(v.w);
         *reinterpret_cast<uint2*>(M.xh[0] + o) = make_uint2(hi_pair(t0, t1), hi_pair(t2, t3));
-        *reinterpret_cast<uint32_t*>(M.xq + o) = code_quad(r0, r1, r2, r3);
+        *reinterpret_cast<uint32_t*>(M.xq + o) = code_quad(t0, t1, t2, t3);
     } else if (outputs & (kPrepBF16 | kPrepBF16Lo)) {
         uint2 h;
         h.x = pack2(v.x, v.y);

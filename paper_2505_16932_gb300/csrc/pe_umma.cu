@@ -464,13 +464,13 @@ __device__ __forceinline__ void stage_x_row(uint8_t* s_h, uint8_t* s_q, int r, c
     uint32_t qw[8];
 #pragma unroll
     for (int c8 = 0; c8 < 4; ++c8) {
-        uint32_t t[8], rr[8];
+        uint32_t t[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) x_split(v[8 * c8 + k], t[k], rr[k]);
+        for (int k = 0; k < 8; ++k) t[k] = x_split(v[8 * c8 + k]);
         *reinterpret_cast<uint4*>(s_h + bf16_off(r, 8 * c8)) =
             make_uint4(hi_pair(t[0], t[1]), hi_pair(t[2], t[3]), hi_pair(t[4], t[5]), hi_pair(t[6], t[7]));
-        qw[2 * c8] = code_quad(rr[0], rr[1], rr[2], rr[3]);
-        qw[2 * c8 + 1] = code_quad(rr[4], rr[5], rr[6], rr[7]);
+        qw[2 * c8] = code_quad(t[0], t[1], t[2], t[3]);
+        qw[2 * c8 + 1] = code_quad(t[4], t[5], t[6], t[7]);
     }
     *reinterpret_cast<uint4*>(s_q + q8_off(r, 0)) = make_uint4(qw[0], qw[1], qw[2], qw[3]);
     *reinterpret_cast<uint4*>(s_q + q8_off(r, 16)) = make_uint4(qw[4], qw[5], qw[6], qw[7]);
