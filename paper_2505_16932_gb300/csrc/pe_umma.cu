@@ -59,7 +59,6 @@ constexpr int kBN = 256;        // tile width (UMMA N, <= 256)
 // The k-block BK (64 or 32 BF16 elements: one 128- or 64-byte swizzle row)
 // is a template parameter; a smaller k-block gives more, smaller pipeline
 // stages in the same shared memory.
-constexpr int kWarpStage = 10240;        // per epilogue warp staging (BF16 path)
 constexpr uint64_t kDefaultWaitNs = 1000000000ull;  // 1 s
 
 enum MapIdx {
@@ -618,11 +617,17 @@ struct Cfg {
     static constexpr int kBBytes = ((MODE == 2) ? kBN / 2 : kBN) * BK * 2;   // B tile (or half) of one k-block
     static constexpr int kAOps = (NS == 1) ? 1 : 2;   // stage: A hi | [A lo] | B hi | [B lo]
     static constexpr int kStage = kAOps * (kABytes + kBBytes);
-    static constexpr int kStages = (MODE == 2) ? 4 : ((NS == 1) ? 3 : 2) * (64 / BK);
+    static constexpr int kStages = (MODE == 2) ? 5 : ((NS == 1) ? 3 : 2) * (64 / BK);
+    // BF16 epilogue staging per warp: operand prefetch buffers of 3 KB (two,
+    // fetched two chunks ahead; one in the 2-SM kernel, whose smem goes to a
+    // fifth operand stage) and a 4 KB output box
+    static constexpr int kNpf = (MODE == 2) ? 1 : 2;
+    static constexpr int kWarpStage = 4096 + 3072 * kNpf;
     static constexpr uint32_t kSwzK = (BK == 64) ? 2u : 4u;   // K-major operand swizzle
     static constexpr uint32_t kSboK = 8 * BK * 2;             // 8 rows of one k-block
     static constexpr int kEpiOff = kStages * kStage;
     static constexpr int kBarOff = kEpiOff + ((NS == 1) ? kEpiWarps * kWarpStage : 0);
+    static_assert(kWarpStage % 1024 == 0, "staging boxes need 1024-byte alignment");
     static constexpr size_t kSmem = 1024 + kBarOff + 512;
 };
 
@@ -890,12 +895,16 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
         const int q = warp & 3;            // TMEM lane quarter = the warp's 32 tile rows
         const int grp = ew >> 2;           // column half of the tile
         const int etid = threadIdx.x - 64; // 0..255
-        uint8_t* stg = smem + C::kEpiOff + ew * kWarpStage;
+        constexpr int NPF = C::kNpf;
+        uint8_t* stg = smem + C::kEpiOff + ew * C::kWarpStage;
         // staging: two operand buffers (X hi at +0 and code at +2048, or
         // BF16 A) of 3 KB, then the output box: X hi + code (update), FP32
         // or BF16 result (last update), BF16 direct + mirror (symmetric)
-        uint8_t* s_out = stg + 6144;
-        uint32_t pf_issued = 0, pf_used = 0;   // operand prefetches, in order: buffer n & 1, parity (n >> 1) & 1
+        uint8_t* s_out = stg;                  // output box (4 KB, first: 1024-byte aligned)
+        uint8_t* s_pf = stg + 4096;            // operand buffer b at s_pf + 3072 b
+        // operand prefetches, issued and consumed in order: prefetch n uses
+        // buffer n % NPF, whose barrier completes phase n / NPF
+        uint32_t pf_issued = 0, pf_used = 0;
         int acc = 0;
         uint32_t acc_phase = 0;
         long long c_tfull = 0, c_dep = 0, c_gram = 0, c_sq = 0, c_ap = 0, c_rdx = 0, c_pf = 0, c_math = 0, c_st = 0, c_fn = 0,
@@ -950,13 +959,13 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             const float* in_g = (NS == 1) ? nullptr
                                 : (g.kind == kApply) ? M.xf + (int64_t)gi * M.Lp : M.af + (int64_t)gi * M.sp;
             // BF16 path: the epilogue operand (update: X hi + code, square:
-            // BF16 A) of each stored chunk is fetched by TMA two chunks ahead
+            // BF16 A) of each stored chunk is fetched by TMA NPF chunks ahead
             const CUtensorMap* in_map = mp + ((g.kind == kApply) ? (A.cur ? kMapEXH1 : kMapEXH0) : kMapEAH);
             const uint32_t in_bytes = (g.kind == kApply) ? 3072u : 2048u;
             auto prefetch = [&](int ch) {
-                const int b = pf_issued & 1;
+                const int b = (NPF == 2) ? (int)(pf_issued & 1) : 0;
                 if (lane == 0) {
-                    const uint32_t dst = smem_u32(stg + b * 3072);
+                    const uint32_t dst = smem_u32(s_pf + b * 3072);
                     mbar_expect_tx(&pfbar[2 * ew + b], in_bytes);
                     tma_load_2d(dst, in_map, &pfbar[2 * ew + b], cb + ch * 32, gi0);
                     if (g.kind == kApply) tma_load_2d(dst + 2048, mp + kMapEXQ, &pfbar[2 * ew + b], cb + ch * 32, gi0);
@@ -966,7 +975,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             if (NS == 1) {
                 if (needs_in) {
                     if (first < nch) prefetch(first);
-                    if (first + 1 < nch) prefetch(first + 1);
+                    if (NPF == 2 && first + 1 < nch) prefetch(first + 1);
                 }
             } else if (needs_in && first < nch) {
                 load32(pre, in_g + cb + first * 32);
@@ -998,12 +1007,21 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                 if (sub) { const long long t = clock64(); c_tm += t - s0c; s0c = t; }
                 if (NS == 1) {
                     if (needs_in) {
-                        const int b = pf_used & 1;
-                        mbar_wait(&pfbar[2 * ew + b], (pf_used >> 1) & 1, limit, nullptr);
+                        const int b = (NPF == 2) ? (int)(pf_used & 1) : 0;
+                        const uint32_t par = (NPF == 2) ? ((pf_used >> 1) & 1) : (pf_used & 1);
+                        mbar_wait(&pfbar[2 * ew + b], par, limit, nullptr);
                         if (sub) { const long long t = clock64(); c_pf += t - s0c; s0c = t; }
-                        if (g.kind == kApply) read_x_row(stg + b * 3072, lane, pre);
-                        else read_bf16_row(stg + b * 3072, lane, pre);
+                        if (g.kind == kApply) read_x_row(s_pf + b * 3072, lane, pre);
+                        else read_bf16_row(s_pf + b * 3072, lane, pre);
                         ++pf_used;
+                        if (NPF == 1) {
+                            // single buffer: refill it for the next chunk as soon as
+                            // every lane has read it (async-proxy write after
+                            // generic-proxy reads: fence, then the issue)
+                            fence_async_smem();
+                            __syncwarp();
+                            if (i + 1 < nch) prefetch(i + 1);
+                        }
                     }
                     if (g.kind == kApply) {
                         if (A.step == 0) {
@@ -1093,7 +1111,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                         }
                         bulk_commit();
                     }
-                    if (needs_in && i + 2 < nch) prefetch(i + 2);
+                    if (NPF == 2 && needs_in && i + 2 < nch) prefetch(i + 2);
                     if (sub) { __syncwarp(); c_is += clock64() - s0c; }
                 } else {
                     float nxt_pre[32];
@@ -1130,7 +1148,10 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             if (++acc == NACC) { acc = 0; acc_phase ^= 1; }
         }
         // operand prefetches still in flight (a tile left early) land before exit
-        for (; pf_used < pf_issued; ++pf_used) mbar_wait(&pfbar[2 * ew + (pf_used & 1)], (pf_used >> 1) & 1, limit, nullptr);
+        for (; pf_used < pf_issued; ++pf_used) {
+            if (NPF == 2) mbar_wait(&pfbar[2 * ew + (pf_used & 1)], (pf_used >> 1) & 1, limit, nullptr);
+            else mbar_wait(&pfbar[2 * ew], pf_used & 1, limit, nullptr);
+        }
         if (NS == 1 && lane == 0) bulk_wait0();
         if (prof && etid == 0) {
             prof[kPTFullWait] += c_tfull;
