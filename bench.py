@@ -369,15 +369,16 @@ def main():
 
     # -------------------------------------------------- end-to-end pass
     e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for _ in range(max(1, args.warmup)):   # builds and tunes the per-group plans outside the timed region
+        pe.pe_polar_batched_host(host_in, host_out, table, dtype)
+    torch.cuda.synchronize()
     barrier()
     for k in range(args.steps):
         flush.fill_(1.0)
         e2e_ev[k][0].record(stream)
-        for d, h in zip(dev_x, host_in):
-            d.copy_(h, non_blocking=True)
-        pe.pe_polar_batched(dev_x, table, dtype, flags=flags)
-        for h, d in zip(host_out, dev_x):
-            h.copy_(d, non_blocking=True)
+        # the C ABI's host-buffer entry: copies in, grouped compute, copies
+        # out, pipelined by the library across groups of matrices
+        pe.pe_polar_batched_host(host_in, host_out, table, dtype)
         e2e_ev[k][1].record(stream)
     barrier()
     e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev))

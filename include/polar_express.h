@@ -194,6 +194,24 @@ int pe_polar_batched_ex(void* const* X, const int64_t* m, const int64_t* n, int 
  */
 int pe_sync_status(void* stream);
 
+/* Host-buffer form of pe_polar_batched (FP32, fixed normalisation 1.01 /
+ * 1e-7): Hin[i] (read) and Hout[i] (written) are host m[i] x n[i] row-major
+ * FP32 matrices; pinned memory (cudaHostAlloc / torch pin_memory) lets the
+ * copies run asynchronously at full link bandwidth. The library keeps device
+ * staging buffers per shape set (4 sets, LRU; pe_release frees them) and
+ * pipelines: the matrices are cut into `ngroups` contiguous groups of about
+ * equal bytes (0 = automatic: 4 for >= 8 matrices, 2 for 2-7, else 1); group
+ * g's host->device copies run on one internal stream, its grouped compute on
+ * `stream` once they have landed, its device->host copies on a second
+ * internal stream, so copies in both directions overlap compute of other
+ * groups. All work is ordered after what is already queued on `stream`, and
+ * `stream` waits for the last copy, so synchronising `stream` means Hout is
+ * complete. Calls that share a shape set must not overlap in time (they share
+ * the staging buffers). Errors: as pe_polar_batched, PE_ENOMEM for the
+ * staging buffers. Results are those of pe_polar_batched on the same data. */
+int pe_polar_batched_host(const void* const* Hin, void* const* Hout, const int64_t* m, const int64_t* n, int count,
+                          const double* table, int T, int dtype, int ngroups, void* stream);
+
 /* Number of this library's kernels enqueued (directly or inside replayed
  * graphs) on the calling process since load; for launch accounting. */
 int64_t pe_launch_count(void);

@@ -80,6 +80,8 @@ def lib() -> ctypes.CDLL:
         "pe_debug_set": (c_i, [c_i, c_i64]),
         "pe_trace_enable": (c_i, [c_i]),
         "pe_trace_read": (c_i, [P_i64, P_d, c_i]),
+        "pe_polar_batched_host": (c_i, [ctypes.POINTER(c_p), ctypes.POINTER(c_p), P_i64, P_i64, c_i, P_d, c_i, c_i,
+                                        c_i, c_p]),
         "pe_muon_batched": (c_i, [ctypes.POINTER(c_p), ctypes.POINTER(c_p), ctypes.POINTER(c_p), P_i64, P_i64, c_i,
                                   c_d, c_d, P_d, c_i, c_i, c_u, c_p]),
         "pe_split_open": (c_i, [c_p, c_i64, c_i64, c_i, P_d, c_i, c_i, c_p, ctypes.POINTER(c_p)]),
@@ -201,6 +203,31 @@ def pe_polar_batched(Xs: Sequence, table, dtype: str = "bf16", stream=None, flag
                                      ctypes.c_void_p(_stream_handle(stream)))
     _check(code)
     return Xs
+
+
+def pe_polar_batched_host(H_in: Sequence, H_out: Sequence, table, dtype: str = "bf16", ngroups: int = 0,
+                          stream=None):
+    """Host-buffer form: H_in / H_out are lists of contiguous float32 CPU
+    tensors (pinned for asynchronous copies) of equal shapes per index. The
+    copies are pipelined with the grouped compute on ``stream``."""
+    n = len(H_in)
+    if n == 0:
+        return H_out
+    if len(H_out) != n:
+        raise PolarExpressError(PE_EINVAL, "H_in and H_out must have the same length")
+    for a, b in zip(H_in, H_out):
+        for t in (a, b):
+            if t.is_cuda or t.dim() != 2 or not t.is_contiguous() or _io_of(t) != PE_IO_FP32:
+                raise PolarExpressError(PE_EINVAL, "host matrices must be contiguous 2-D float32 CPU tensors")
+        if a.shape != b.shape:
+            raise PolarExpressError(PE_EINVAL, "H_in and H_out must have the same shapes")
+    arr = lambda ts: (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
+    ms = (ctypes.c_int64 * n)(*[t.shape[0] for t in H_in])
+    ns = (ctypes.c_int64 * n)(*[t.shape[1] for t in H_in])
+    tab = _table(table)
+    _check(lib().pe_polar_batched_host(arr(H_in), arr(H_out), ms, ns, n, _dptr(tab), tab.shape[0], DTYPES[dtype],
+                                       int(ngroups), ctypes.c_void_p(_stream_handle(stream))))
+    return H_out
 
 
 def pe_muon_batched(Ws: Sequence, Gs: Sequence, Ms: Sequence, beta: float, lr: float, table,

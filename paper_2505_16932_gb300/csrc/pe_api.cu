@@ -654,6 +654,136 @@ int run(void* const* X, const int64_t* m, const int64_t* n, const int64_t* ld, i
     return PE_OK;
 }
 
+// ---------------------------------------------------- host-buffer entry
+// pe_polar_batched_host: device staging buffers per shape set, and the copies
+// pipelined with the grouped compute: group g's host->device copies run on
+// one copy stream, its compute on the caller's stream once they land, and its
+// device->host copies on a second copy stream, so the link works in both
+// directions while the tensor cores work on another group.
+
+struct HostPlan {
+    int dev = 0;
+    std::vector<int64_t> dims;       // m, n per matrix
+    std::vector<size_t> off;         // byte offset of matrix i in mem
+    char* mem = nullptr;
+    cudaStream_t c_in = nullptr, c_out = nullptr;
+    std::vector<cudaEvent_t> ev;     // start, done, and 2 per group
+    ~HostPlan() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (c_in) cudaStreamDestroy(c_in);
+        if (c_out) cudaStreamDestroy(c_out);
+        if (mem) cudaFree(mem);
+    }
+};
+std::list<std::unique_ptr<HostPlan>> g_hplans;
+constexpr size_t kMaxHostPlans = 4;
+
+int host_plan(const std::vector<int64_t>& dims, int ngroups, HostPlan** out) {
+    int dev = 0;
+    PE_CU(cudaGetDevice(&dev));
+    for (auto it = g_hplans.begin(); it != g_hplans.end(); ++it) {
+        if ((*it)->dev == dev && (*it)->dims == dims && (int)(*it)->ev.size() >= 2 + 2 * ngroups) {
+            g_hplans.splice(g_hplans.begin(), g_hplans, it);
+            *out = g_hplans.front().get();
+            return PE_OK;
+        }
+    }
+    auto H = std::make_unique<HostPlan>();
+    H->dev = dev;
+    H->dims = dims;
+    size_t tot = 0;
+    for (size_t i = 0; i < dims.size() / 2; ++i) {
+        H->off.push_back(tot);
+        tot += round_up((size_t)(dims[2 * i] * dims[2 * i + 1]) * sizeof(float), 256);
+    }
+    if (g_dbg_fail_alloc) {
+        g_dbg_fail_alloc = false;
+        return fail(PE_ENOMEM, "staging allocation failed (injected)");
+    }
+    cudaError_t e = cudaMalloc(&H->mem, tot);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        H->mem = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? PE_ENOMEM : PE_ECUDA,
+                    std::string("staging allocation of ") + std::to_string(tot) + " bytes failed");
+    }
+    PE_CU(cudaStreamCreateWithFlags(&H->c_in, cudaStreamNonBlocking));
+    PE_CU(cudaStreamCreateWithFlags(&H->c_out, cudaStreamNonBlocking));
+    H->ev.assign(2 + 2 * std::max(ngroups, 4), nullptr);
+    for (cudaEvent_t& ev : H->ev) PE_CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    g_hplans.emplace_front(std::move(H));
+    while (g_hplans.size() > kMaxHostPlans) {
+        cudaDeviceSynchronize();
+        g_hplans.pop_back();
+    }
+    *out = g_hplans.front().get();
+    return PE_OK;
+}
+
+int run_host(const void* const* Hin, void* const* Hout, const int64_t* m, const int64_t* n, int count,
+             const double* table, int T, int dtype, int ngroups, void* stream) {
+    if (!Hin || !Hout || !m || !n) return fail(PE_EINVAL, "NULL argument");
+    if (count < 1 || count > kMaxMatrices) return fail(PE_EINVAL, "count must be in 1..4096");
+    if (ngroups < 0) return fail(PE_EINVAL, "ngroups must be >= 0");
+    std::vector<int64_t> dims(2 * count);
+    size_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        if (!Hin[i] || !Hout[i]) return fail(PE_EINVAL, "host pointer " + std::to_string(i) + " is NULL");
+        if (m[i] < 1 || n[i] < 1) return fail(PE_EINVAL, "sizes must be >= 1");
+        if (m[i] > (1 << 20) || n[i] > (1 << 20) || m[i] * n[i] > (int64_t)1 << 31)
+            return fail(PE_EINVAL, "matrix too large (m, n <= 2^20, m*n <= 2^31)");
+        dims[2 * i] = m[i];
+        dims[2 * i + 1] = n[i];
+        total += (size_t)(m[i] * n[i]);
+    }
+    const int ng = std::min(count, ngroups > 0 ? ngroups : (count >= 8 ? 4 : (count >= 2 ? 2 : 1)));
+    // contiguous groups balanced by bytes
+    std::vector<int> cut(ng + 1, count);
+    cut[0] = 0;
+    {
+        size_t acc = 0;
+        int g = 1;
+        for (int i = 0; i < count && g < ng; ++i) {
+            acc += (size_t)(m[i] * n[i]);
+            if (acc * ng >= total * g && i + 1 < count) cut[g++] = i + 1;
+        }
+        for (; g < ng; ++g) cut[g] = count;   // fewer usable cuts than groups: empty groups
+    }
+    HostPlan* H = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        int r = host_plan(dims, ng, &H);
+        if (r != PE_OK) return r;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    PE_CU(cudaEventRecord(H->ev[0], st));
+    PE_CU(cudaStreamWaitEvent(H->c_in, H->ev[0], 0));
+    PE_CU(cudaStreamWaitEvent(H->c_out, H->ev[0], 0));
+    std::vector<void*> dptr(count);
+    for (int i = 0; i < count; ++i) dptr[i] = H->mem + H->off[i];
+    for (int g = 0; g < ng; ++g) {
+        const int a = cut[g], b = cut[g + 1];
+        if (a >= b) continue;
+        for (int i = a; i < b; ++i)
+            PE_CU(cudaMemcpyAsync(dptr[i], Hin[i], (size_t)(m[i] * n[i]) * sizeof(float), cudaMemcpyHostToDevice,
+                                  H->c_in));
+        PE_CU(cudaEventRecord(H->ev[2 + 2 * g], H->c_in));
+        PE_CU(cudaStreamWaitEvent(st, H->ev[2 + 2 * g], 0));
+        int r = run(dptr.data() + a, m + a, n + a, nullptr, b - a, PE_IO_FP32, table, T, dtype, 1.01, 1e-7, 0,
+                    stream);
+        if (r != PE_OK) return r;
+        PE_CU(cudaEventRecord(H->ev[3 + 2 * g], st));
+        PE_CU(cudaStreamWaitEvent(H->c_out, H->ev[3 + 2 * g], 0));
+        for (int i = a; i < b; ++i)
+            PE_CU(cudaMemcpyAsync(Hout[i], dptr[i], (size_t)(m[i] * n[i]) * sizeof(float), cudaMemcpyDeviceToHost,
+                                  H->c_out));
+    }
+    PE_CU(cudaEventRecord(H->ev[1], H->c_out));
+    PE_CU(cudaStreamWaitEvent(st, H->ev[1], 0));
+    return PE_OK;
+}
+
 // ------------------------------------------------------ long-side split
 // One rank's block of a matrix split along its long side (pe_split_*): a
 // dedicated single-matrix plan (orientation fixed by the caller, phased
@@ -852,6 +982,11 @@ int pe_polar_batched_ex(void* const* X, const int64_t* m, const int64_t* n, int 
                    stream);
 }
 
+int pe_polar_batched_host(const void* const* Hin, void* const* Hout, const int64_t* m, const int64_t* n, int count,
+                          const double* table, int T, int dtype, int ngroups, void* stream) {
+    return pe::run_host(Hin, Hout, m, n, count, table, T, dtype, ngroups, stream);
+}
+
 int pe_sync_status(void* stream) {
     std::lock_guard<std::mutex> lk(pe::g_mu);
     pe::DeviceState* d = nullptr;
@@ -908,8 +1043,9 @@ const char* pe_last_error(void) { return pe::g_err.c_str(); }
 
 void pe_release(void) {
     std::lock_guard<std::mutex> lk(pe::g_mu);
-    if (!pe::g_plans.empty()) cudaDeviceSynchronize();
+    if (!pe::g_plans.empty() || !pe::g_hplans.empty()) cudaDeviceSynchronize();
     pe::g_plans.clear();
+    pe::g_hplans.clear();
 }
 
 int pe_split_open(void* X, int64_t rows, int64_t cols, int short_is_rows, const double* table, int T, int dtype,

@@ -120,3 +120,16 @@ def test_split_argument_errors_without_gpu(L):
     assert L.pe_split_gram(None, 0, fake, 4) == pe.PE_EINVAL
     assert L.pe_split_step(None, 0, fake, 4) == pe.PE_EINVAL
     assert L.pe_split_close(None) == pe.PE_EINVAL
+
+
+def test_host_entry_argument_errors_without_gpu(L):
+    tab = np.ones((5, 3))
+    P = ctypes.POINTER(ctypes.c_double)
+    tp = tab.ctypes.data_as(P)
+    ms = (ctypes.c_int64 * 1)(4)
+    ptrs = (ctypes.c_void_p * 1)(None)
+    assert L.pe_polar_batched_host(None, None, ms, ms, 1, tp, 5, pe.PE_BF16, 0, None) == pe.PE_EINVAL
+    assert L.pe_polar_batched_host(ptrs, ptrs, ms, ms, 1, tp, 5, pe.PE_BF16, 0, None) == pe.PE_EINVAL
+    assert L.pe_polar_batched_host(ptrs, ptrs, ms, ms, 0, tp, 5, pe.PE_BF16, 0, None) == pe.PE_EINVAL
+    fake = (ctypes.c_void_p * 1)(0x10000)
+    assert L.pe_polar_batched_host(fake, fake, ms, ms, 1, tp, 5, pe.PE_BF16, -1, None) == pe.PE_EINVAL

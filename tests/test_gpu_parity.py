@@ -362,3 +362,28 @@ def test_degree3_tables_skip_square(which):
             for X, G in zip(Xs, mats):
                 ref = O.polar_express(G.astype(np.float32).astype(np.float64), tab)
                 assert O.rel_fro(X.cpu().numpy().astype(np.float64), ref) <= tol, (dtype, flags, G.shape)
+
+
+# ------------------------------------------------------- host-buffer entry
+
+@pytest.mark.parametrize("ngroups", [0, 1, 2, 3])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffers_equal_device_call(ngroups, pinned):
+    """pe_polar_batched_host pipelines the copies with the grouped compute;
+    the grouping does not change the bits (grouped == single), so the result
+    equals pe_polar_batched on device copies of the same inputs."""
+    mats = _uneven(seed=17) + _even(seed=18)[:2]
+    tab = table(1e-3, 5)
+    H_in = [torch.from_numpy(np.ascontiguousarray(G, dtype=np.float32)) for G in mats]
+    if pinned:
+        H_in = [h.pin_memory() for h in H_in]
+    H_out = [torch.empty_like(h) for h in H_in]
+    if pinned:
+        H_out = [h.pin_memory() for h in H_out]
+    pe.pe_polar_batched_host(H_in, H_out, tab, "bf16", ngroups=ngroups)
+    pe.pe_sync_status()
+    Xs = [h.cuda() for h in H_in]
+    pe.pe_polar_batched(Xs, tab, "bf16")
+    pe.pe_sync_status()
+    for h, X in zip(H_out, Xs):
+        assert torch.equal(h, X.cpu())
