@@ -166,6 +166,31 @@ def cpu_cores():
     return os.cpu_count() or 1
 
 
+def accuracy_sample(wl):
+    """Indices of the accuracy sample: the first matrix of each distinct shape (up to 4)."""
+    seen = {}
+    for i, sh in enumerate(wl.shapes):
+        seen.setdefault(sh, i)
+    return list(seen.values())[:4]
+
+
+def cpu_baseline_leg(wl, table, budget_s: float, acc_idx):
+    """The leg of this script that runs the FP64 oracle: its timing on the
+    host cores (oracle_sample) and the FP64 iterates of the accuracy sample
+    (the spectral form where the factors are known, else the iteration on the
+    FP32-cast input), with the true polar factors. Returns (timing, refs)."""
+    import oracle as O
+    refs = {}
+    for i in acc_idx:
+        sv = wl.svd[i]
+        if sv is not None:
+            refs[i] = (O.polar_express_spectral(sv.U, sv.s, sv.V, table), sv.U @ sv.V.T)
+        else:
+            G = wl.matrices[i]
+            refs[i] = (O.polar_express(G.astype(np.float32).astype(np.float64), table), O.polar_svd(G))
+    return oracle_sample(wl, table, budget_s), refs
+
+
 def oracle_sample(wl, table, budget_s: float):
     """Time the FP64 oracle iteration over the workload's matrices in order
     until `budget_s` has elapsed (at least one matrix). Returns
@@ -275,6 +300,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP32 comparison and accuracy sample")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-largest", action="store_true", help="skip the largest-configuration measurement")
+    ap.add_argument("--sweep", action="store_true",
+                    help="error vs iteration count and vs time for FP32, BF16, BF16x3 and Newton-Schulz "
+                         "(ill-conditioned workload)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -422,11 +450,15 @@ def main():
     extras = {}
     cpu = None
     if rank == 0:
+        acc_idx = [] if args.no_extras else accuracy_sample(wl)
+        (tf, secs, done), refs = cpu_baseline_leg(wl, table, args.cpu_budget, acc_idx)
         if not args.no_extras:
-            extras = accuracy_and_fp32(pe, torch, wl, table, dev_in, dtype, flush, stream, args)
+            extras = accuracy_and_fp32(pe, torch, wl, table, dev_in, dtype, flush, stream, args, refs)
+            extras["newton_schulz5"] = newton_schulz_line(pe, torch, wl, dev_in, dtype, flush, stream, refs, args)
+        if args.sweep or wl.name == "ill_conditioned":
+            extras["error_vs_T"] = error_sweep(pe, torch, wl, dev_in, flush, stream)
         if not args.no_largest and wl.name != "large_dense" and world == 1:
             extras["largest_config"] = largest_config(pe, torch, flush, stream, min(args.steps, 10))
-        tf, secs, done = oracle_sample(wl, table, args.cpu_budget)
         cpu = {"value": tf, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
                "sample": f"FP64 numpy oracle iteration of the first {done} of {len(shapes)} matrices, "
                          f"T={T} ({secs:.1f} s)"}
@@ -545,10 +577,98 @@ def largest_config(pe, torch, flush, stream, steps):
     return out
 
 
-def accuracy_and_fp32(pe, torch, wl, table, dev_in, dtype, flush, stream, args):
-    """FP32 plain path on the same workload (time per step) and errors of a
-    sample of matrices (one of each shape) against the FP64 oracle."""
-    import oracle as O
+NS5_ROW = (15.0 / 8.0, -10.0 / 8.0, 3.0 / 8.0)   # the fixed Newton-Schulz quintic (Sec. 2)
+
+
+def newton_schulz_line(pe, torch, wl, dev_in, dtype, flush, stream, refs, args):
+    """The fixed-coefficient Newton-Schulz quintic, T = the workload's T, run
+    through the same kernels (same grouped call and graph): time per step and
+    max|sigma - 1| on the accuracy sample."""
+    table = np.array([NS5_ROW] * wl.T)
+    xs = [d.clone() for d in dev_in]
+    for _ in range(2):
+        for d, s in zip(xs, dev_in):
+            d.copy_(s)
+        pe.pe_polar_batched(xs, table, dtype)
+    n = max(3, min(20, args.steps // 5))
+    tot = 0.0
+    for _ in range(n):
+        for d, s in zip(xs, dev_in):
+            d.copy_(s)
+        flush.fill_(3.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pe.pe_polar_batched(xs, table, dtype)
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    ms = tot / n
+    errs = [_max_sigma_err(xs[i].cpu().numpy().astype(np.float64)) for i in sorted(refs)]
+    pe_errs = [_max_sigma_err(refs[i][0]) for i in sorted(refs)]
+    return {"value": algorithmic_flops(wl.shapes, wl.T) / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
+            "T": wl.T, "dtype": dtype, "max_sigma_err_sample": max(errs) if errs else None,
+            "polar_express_fp64_max_sigma_err_sample": max(pe_errs) if pe_errs else None}
+
+
+def error_sweep(pe, torch, wl, dev_in, flush, stream, Ts=(2, 4, 6, 8, 10, 12), gamma=1e-3):
+    """Error against the truth U V^T vs iteration count T and vs time, for the
+    Polar Express tables (FP32 plain, BF16, BF16x3) and the Newton-Schulz
+    quintic (BF16), on a workload with known factors. Errors per T: the
+    largest over the workload's matrices of max|sigma_i - 1| restricted to the
+    directions with s_i >= gamma s_max (singular values of U1^T X V1, FP64 on
+    the GPU) and of ||X - U V^T||_F / sqrt(n)."""
+    kept = []
+    for sv in wl.svd:
+        k = sv.s >= gamma * sv.s.max()
+        U = torch.from_numpy(sv.U).cuda()
+        V = torch.from_numpy(sv.V).cuda()
+        kept.append((U[:, k].contiguous(), V[:, k].contiguous(), U, V))
+    rows = []
+    for T in Ts:
+        for path in ("fp32", "bf16", "bf16x3", "ns5"):
+            table = np.array([NS5_ROW] * T) if path == "ns5" else pe.pe_coeffs(5, wl.l, T, 1.01)
+            dt = "bf16" if path == "ns5" else path
+            xs = [d.clone() for d in dev_in]
+            pe.pe_polar_batched(xs, table, dt)            # plan, tuning
+            ms = 0.0
+            for _ in range(3):
+                for d, s in zip(xs, dev_in):
+                    d.copy_(s)
+                flush.fill_(4.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                pe.pe_polar_batched(xs, table, dt)
+                b.record(stream)
+                b.synchronize()
+                ms += a.elapsed_time(b) / 3
+            rmax, efro = 0.0, 0.0
+            for X, (U1, V1, U, V) in zip(xs, kept):
+                Xd = X.double()
+                sig = torch.linalg.svdvals(U1.T @ Xd @ V1)
+                rmax = max(rmax, float((sig - 1).abs().max()))
+                efro = max(efro, float(torch.linalg.norm(Xd - U @ V.T) / np.sqrt(min(X.shape))))
+            rows.append({"path": path, "T": T, "ms": ms, "restricted_max_sigma_err": rmax,
+                         "err_fro_per_sqrt_n": efro})
+            del xs
+    return {"gamma": gamma, "rows": rows}
+
+
+def _rel_fro(X, Y):
+    return float(np.linalg.norm(X - Y) / np.linalg.norm(Y))
+
+
+def _err_fro(X, P):
+    return float(np.linalg.norm(X - P) / np.sqrt(min(X.shape)))
+
+
+def _max_sigma_err(X):
+    return float(np.max(np.abs(np.linalg.svd(X, compute_uv=False) - 1.0)))
+
+
+def accuracy_and_fp32(pe, torch, wl, table, dev_in, dtype, flush, stream, args, refs):
+    """FP32 plain path on the same workload (time per step) and errors of the
+    accuracy sample against the FP64 iterates ``refs`` that the cpu_baseline
+    leg computed."""
     out = {}
     xs = [d.clone() for d in dev_in]
     # FP32 plain timing
@@ -570,11 +690,7 @@ def accuracy_and_fp32(pe, torch, wl, table, dev_in, dtype, flush, stream, args):
         tot += a.elapsed_time(b)
     ms32 = tot / n
     flops = algorithmic_flops(wl.shapes, wl.T)
-    # accuracy sample: first matrix of each distinct shape
-    seen = {}
-    for i, sh in enumerate(wl.shapes):
-        seen.setdefault(sh, i)
-    idx = list(seen.values())[:4]
+    idx = sorted(refs)
     res = {}
     for path in (dtype, "fp32"):
         xs2 = [dev_in[i].clone() for i in idx]
@@ -583,16 +699,10 @@ def accuracy_and_fp32(pe, torch, wl, table, dev_in, dtype, flush, stream, args):
         errs = []
         for j, i in enumerate(idx):
             got = xs2[j].cpu().numpy().astype(np.float64)
-            sv = wl.svd[i]
-            if sv is not None:
-                ref = O.polar_express_spectral(sv.U, sv.s, sv.V, table)
-                P = sv.U @ sv.V.T
-            else:
-                ref = O.polar_express(wl.matrices[i].astype(np.float32).astype(np.float64), table)
-                P = O.polar_svd(wl.matrices[i])
-            errs.append({"shape": list(wl.shapes[i]), "rel_fro_vs_fp64_iteration": O.rel_fro(got, ref),
-                         "err_fro_per_sqrt_n": O.err_polar_fro(got, P), "max_sigma_err": O.max_sigma_err(got),
-                         "fp64_max_sigma_err": O.max_sigma_err(ref)})
+            ref, P = refs[i]
+            errs.append({"shape": list(wl.shapes[i]), "rel_fro_vs_fp64_iteration": _rel_fro(got, ref),
+                         "err_fro_per_sqrt_n": _err_fro(got, P), "max_sigma_err": _max_sigma_err(got),
+                         "fp64_max_sigma_err": _max_sigma_err(ref)})
         res[path] = errs
     worst16 = max(e["max_sigma_err"] for e in res[dtype])
     worst32 = max(e["max_sigma_err"] for e in res["fp32"])
