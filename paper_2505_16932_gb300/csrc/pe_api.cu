@@ -270,7 +270,7 @@ int build_plan(const PlanKey& key, Plan** out) {
     P->n_prep = (int)prep.size();
     const size_t o_part = cv.take(sizeof(double) * prep.size(), 64);
     const size_t o_nscale = cv.take(sizeof(float) * count, 64);
-    const size_t o_ticket = cv.take(64, 64);
+    const size_t o_ticket = cv.take(sizeof(unsigned) * count, 64);   // prepare: one ticket per matrix
     const size_t o_prep = cv.take(sizeof(TileTask) * prep.size(), 64);
     size_t o_tl[3];
     for (int k = 0; k < 3; ++k) {
@@ -330,8 +330,14 @@ int build_plan(const PlanKey& key, Plan** out) {
     P->d_prep = reinterpret_cast<TileTask*>(base + o_prep);
     for (int k = 0; k < 3; ++k) P->d_tiles[k] = reinterpret_cast<TileTask*>(base + o_tl[k]);
     P->d_counters = reinterpret_cast<int*>(base + o_cnt);
+    // zero the whole workspace once: the padding of every canonical buffer
+    // stays zero from here on (prepare skips strips of padding rows), and the
+    // tickets and counters start at zero
+    PE_CU(cudaMemset(P->ws, 0, P->ws_bytes));
+    for (int i = 0; i < count; ++i)
+        if (P->mats[i].xq) PE_CU(cudaMemset(P->mats[i].xq, 0x80, (size_t)P->mats[i].sp * P->mats[i].Lp));   // code of 0
     PE_CU(cudaMemcpy(P->d_mats, P->mats.data(), sizeof(DevMat) * count, cudaMemcpyHostToDevice));
-    PE_CU(cudaMemset(P->d_ticket, 0, 64));
+
     PE_CU(cudaMemcpy(P->d_prep, prep.data(), sizeof(TileTask) * prep.size(), cudaMemcpyHostToDevice));
     for (int k = 0; k < 3; ++k)
         if (!tl[k].empty())
@@ -372,6 +378,7 @@ int enqueue(Plan* P, cudaStream_t st, bool tuning = false) {
     if (k.dtype == PE_BF16X3) outputs = kPrepF32 | kPrepBF16 | kPrepBF16Lo;
     if (!k.w.empty()) outputs |= kPrepMuon;                              // fused Muon step: momentum in prepare
     if (tuning) outputs |= kPrepNoMom;                                    // a tuning run leaves M unchanged
+    outputs |= kPrepSkipPad;
     {
         TraceScope ts(1, st);
         PE_CU(launch_prepare(P->d_mats, k.count, P->d_prep, P->n_prep, P->d_partials, k.scale, k.eps, outputs,
@@ -844,7 +851,7 @@ int split_sumsq(Split* S, double* sumsq) {
     if (!S || !sumsq) return fail(PE_EINVAL, "NULL argument");
     Plan* P = S->plan.get();
     const PlanKey& k = P->key;
-    const int outputs = (k.dtype == PE_BF16) ? kPrepCode : kPrepF32;
+    const int outputs = ((k.dtype == PE_BF16) ? kPrepCode : kPrepF32) | kPrepSkipPad;
     PE_CU(launch_prepare(P->d_mats, 1, P->d_prep, P->n_prep, P->d_partials, k.scale, k.eps, outputs,
                          P->d_nscale, P->ds->status, P->d_counters, P->n_counters, P->d_ticket, S->st));
     S->partials.resize(P->n_prep);

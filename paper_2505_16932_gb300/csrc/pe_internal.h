@@ -14,7 +14,8 @@ constexpr int kMaxMatrices = 4096;
 constexpr int kPadS = 128;
 constexpr int kPadL = 128;
 // The prepare kernel takes one kPrepRows x kPrepCols strip of the padded
-// layout per block (the last strip of a row may be kPadL wide).
+// layout per block (the last strip of a row may be kPadL wide); `ticket` is
+// one counter per matrix, zero between launches.
 constexpr int kPrepRows = 64;
 constexpr int kPrepCols = 256;
 
@@ -74,7 +75,8 @@ enum TileKind { kGram = 0, kSquare = 1, kApply = 2 };
 // Which canonical buffers the prepare kernel fills.
 enum PrepOut { kPrepF32 = 1, kPrepBF16 = 2, kPrepBF16Lo = 4, kPrepCode = 8,
                kPrepNoMom = 16,     // fused Muon: compute the momentum but leave M unchanged (tuning runs)
-               kPrepMuon = 32 };    // fused Muon: the kernel instantiation with the momentum update
+               kPrepMuon = 32,      // fused Muon: the kernel instantiation with the momentum update
+               kPrepSkipPad = 64 }; // skip strips of padding rows (their buffers were zeroed once)
 
 // Final store of element (i, l) of the canonical result X_T: into the
 // caller's matrix, or for a fused Muon step W(i, l) <- W(i, l) - lr X_T(i, l).

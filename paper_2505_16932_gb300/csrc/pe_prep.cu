@@ -136,7 +136,10 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
     // all sixteen loads of a thread are issued before any store (the
     // compiler cannot move loads of G across stores that may alias it)
     float4 ld[16];
-    if (!M.trans) {
+    if ((outputs & kPrepSkipPad) && i0 >= M.s) {
+        // every row of the strip is padding: the workspace holds zeros there
+        // from the plan's creation on, and no step ever writes anything else
+    } else if (!M.trans) {
         // X[i][l] = G[i][l]; G is s x L. 64 threads per row, 4 rows per pass.
         const int c = (tid & 63) * 4, r0 = tid >> 6;
         const bool on = l0 + c < M.Lp;   // the last strip of a row may be 128 wide
@@ -219,18 +222,19 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
         for (int w = 0; w < 8; ++w) s += red[w];
         partials[blockIdx.x] = s;
         __threadfence();
-        const unsigned t = atomicAdd(ticket, 1u);
-        s_last = (t == gridDim.x - 1);
+        const unsigned t = atomicAdd(&ticket[tk.mat], 1u);
+        s_last = (t == (unsigned)M.npart - 1);
     }
     __syncthreads();
     if (!s_last) return;
-    // last block: per-matrix normalisation factors
+    // last strip of this matrix to finish: its normalisation factor (the
+    // matrix's strip partials in a fixed order: 32 strided lane sums, then a
+    // butterfly), and the ticket reset for the next launch
     __threadfence();
-    const int w = tid >> 5, lane = tid & 31;
-    for (int m = w; m < nmats; m += 8) {
-        const DevMat& Mm = mats[m];
+    if (tid < 32) {
+        const int lane = tid, m = tk.mat;
         double s = 0.0;
-        for (int i = lane; i < Mm.npart; i += 32) s += *((volatile double*)&partials[Mm.part0 + i]);
+        for (int i = lane; i < M.npart; i += 32) s += *((volatile double*)&partials[M.part0 + i]);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
             const double nu = sqrt(s);
@@ -243,10 +247,9 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
                 inv = 0.f;
             }
             nscale[m] = inv;
+            ticket[m] = 0u;
         }
     }
-    __syncthreads();
-    if (tid == 0) *ticket = 0u;
 }
 
 // Long-side split: the summed FP32 Gram (s x s, leading dimension lda) into
