@@ -261,6 +261,8 @@ void pe_release(void);
  *          multiple of 256).
  *   key 8: accumulators per CTA of 2-SM plans built from now on (1 or 2;
  *          0 = default).
+ *   key 9: value != 0 turns off the pairing of BF16 matrices with a short
+ *          side <= 64 in plans built from now on (0 = pairing on).
  * Returns PE_EINVAL for an unknown key.
  */
 int pe_debug_set(int key, int64_t value);

@@ -37,6 +37,7 @@ int g_dbg_bk = 0;      // 0: default k-block
 int g_dbg_order = -1;  // -1: default tile order
 int g_dbg_mode = -1;   // -1: autotuned; 0 / 1 / 2: force the tcgen05 kernel mode
 int g_dbg_nacc = 0;    // 0: default accumulators of 2-SM plans; 1 or 2
+bool g_dbg_nopair = false;   // true: no packing of small matrices in plans built from now on
 
 // tracing: (kind, start, stop) event triples recorded on the call's stream
 struct TraceRec { int kind; cudaEvent_t a, b; };
@@ -188,8 +189,49 @@ int build_plan(const PlanKey& key, Plan** out) {
     if (!(P->ds->major == 10 && P->ds->minor == 3))
         return fail(PE_EUNSUPPORTED, "this library is built for sm_103 (GB300) only");
 
-    const int count = key.count;
     const int dtype = key.dtype;
+    // Descriptors: one per matrix, except that on the BF16 path matrices with
+    // a short side <= 64 of one shape are packed, up to kMaxPack, into a
+    // descriptor of kMaxPack 64-row blocks (block k holds matrix k's canonical
+    // rows), and the Gram keeps the diagonal 64 x 64 blocks only, so A,
+    // B = b A + c A^2 and the update stay block diagonal: the pack fills the
+    // MMA tiles that each such matrix alone would pad, and a pack's 256 rows
+    // keep the plan eligible for the 2-SM kernel. A shape seen once is not
+    // packed.
+    std::vector<std::vector<int>> src;   // per descriptor: its matrices
+    {
+        const bool can_pack = dtype == PE_BF16 && key.w.empty() && !(key.flags & kFlagSplit) && !g_dbg_nopair;
+        std::map<std::pair<int64_t, int64_t>, int> shape_n;
+        if (can_pack)
+            for (int i = 0; i < key.count; ++i) {
+                const int64_t m = key.dims[3 * i], n = key.dims[3 * i + 1];
+                if (std::min(m, n) <= 64 && key.dims[3 * i + 2] == n) ++shape_n[{m, n}];
+            }
+        std::map<std::pair<int64_t, int64_t>, int> open;   // shape -> descriptor with room
+        for (int i = 0; i < key.count; ++i) {
+            const int64_t m = key.dims[3 * i], n = key.dims[3 * i + 1];
+            auto sn = shape_n.find({m, n});
+            if (sn != shape_n.end() && sn->second >= 2 && key.dims[3 * i + 2] == n) {
+                auto it = open.find({m, n});
+                if (it != open.end()) {
+                    src[it->second].push_back(i);
+                    if ((int)src[it->second].size() == kMaxPack) open.erase(it);
+                    continue;
+                }
+                open[{m, n}] = (int)src.size();
+            }
+            src.push_back({i});
+        }
+        // a descriptor opened for packing keeps its kMaxPack blocks even if
+        // fewer matrices arrived (the missing blocks are padding)
+        for (auto& d : src)
+            if (d.size() == 1) {
+                const int64_t m = key.dims[3 * d[0]], n = key.dims[3 * d[0] + 1];
+                auto sn = shape_n.find({m, n});
+                if (sn != shape_n.end() && sn->second >= 2) d.push_back(-1);   // marks a pack of one
+            }
+    }
+    const int count = (int)src.size();
     P->mats.resize(count);
     Carve cv;
     // layout of the single workspace allocation
@@ -201,11 +243,17 @@ int build_plan(const PlanKey& key, Plan** out) {
     for (int i = 0; i < count; ++i) {
         DevMat& M = P->mats[i];
         memset(&M, 0, sizeof(M));
-        const int64_t m = key.dims[3 * i], n = key.dims[3 * i + 1], ld = key.dims[3 * i + 2];
-        M.user = reinterpret_cast<void*>(key.ptrs[i]);
+        const int u = src[i][0];
+        const int64_t m = key.dims[3 * u], n = key.dims[3 * u + 1], ld = key.dims[3 * u + 2];
+        M.user = reinterpret_cast<void*>(key.ptrs[u]);
+        if (src[i].size() > 1) {   // a pack
+            M.npack = 1;
+            for (size_t k = 1; k < src[i].size(); ++k)
+                if (src[i][k] >= 0) M.pack[M.npack++ - 1] = reinterpret_cast<void*>(key.ptrs[src[i][k]]);
+        }
         if (!key.w.empty()) {
-            M.mom = reinterpret_cast<float*>(key.mom[i]);
-            M.w = reinterpret_cast<float*>(key.w[i]);
+            M.mom = reinterpret_cast<float*>(key.mom[u]);
+            M.w = reinterpret_cast<float*>(key.w[u]);
             M.beta = key.beta;
             M.lr = key.lr;
         }
@@ -224,6 +272,7 @@ int build_plan(const PlanKey& key, Plan** out) {
             M.L = (int32_t)(M.trans ? m : n);
         }
         M.sp = (int32_t)round_up(M.s, kPadS);
+        if (M.npack) M.sp = 64 * kMaxPack;
         M.Lp = (int32_t)round_up(M.L, kPadL);
         M.part0 = part;
         for (int a = 0; a < M.sp / kPrepRows; ++a)
@@ -232,6 +281,7 @@ int build_plan(const PlanKey& key, Plan** out) {
                 ++part;
             }
         M.npart = part - M.part0;
+        if (M.npack) M.npart /= kMaxPack;   // per 64-row block
         const size_t sL = (size_t)M.sp * M.Lp, ss = (size_t)M.sp * M.sp;
         Off& o = offs[i];
         memset(&o, 0, sizeof(o));
@@ -269,8 +319,8 @@ int build_plan(const PlanKey& key, Plan** out) {
     }
     P->n_prep = (int)prep.size();
     const size_t o_part = cv.take(sizeof(double) * prep.size(), 64);
-    const size_t o_nscale = cv.take(sizeof(float) * count, 64);
-    const size_t o_ticket = cv.take(sizeof(unsigned) * count, 64);   // prepare: one ticket per matrix
+    const size_t o_nscale = cv.take(sizeof(float) * kMaxPack * count, 64);   // per descriptor and block
+    const size_t o_ticket = cv.take(sizeof(unsigned) * kMaxPack * count, 64);   // prepare: per descriptor and block
     const size_t o_prep = cv.take(sizeof(TileTask) * prep.size(), 64);
     size_t o_tl[3];
     for (int k = 0; k < 3; ++k) {
@@ -381,7 +431,7 @@ int enqueue(Plan* P, cudaStream_t st, bool tuning = false) {
     outputs |= kPrepSkipPad;
     {
         TraceScope ts(1, st);
-        PE_CU(launch_prepare(P->d_mats, k.count, P->d_prep, P->n_prep, P->d_partials, k.scale, k.eps, outputs,
+        PE_CU(launch_prepare(P->d_mats, (int)P->mats.size(), P->d_prep, P->n_prep, P->d_partials, k.scale, k.eps, outputs,
                              P->d_nscale, P->ds->status, P->d_counters, P->n_counters, P->d_ticket, st));
     }
     ++nk;
@@ -1114,6 +1164,7 @@ int pe_debug_set(int key, int64_t value) {
         case 6: pe::g_dbg_order = (int)value; return PE_OK;
         case 7: pe::g_dbg_mode = (int)value; return PE_OK;
         case 8: pe::g_dbg_nacc = (int)value; return PE_OK;
+        case 9: pe::g_dbg_nopair = value != 0; return PE_OK;
         default: return pe::fail(PE_EINVAL, "unknown debug key");
     }
 }

@@ -14,10 +14,14 @@ constexpr int kMaxMatrices = 4096;
 constexpr int kPadS = 128;
 constexpr int kPadL = 128;
 // The prepare kernel takes one kPrepRows x kPrepCols strip of the padded
-// layout per block (the last strip of a row may be kPadL wide); `ticket` is
-// one counter per matrix, zero between launches.
+// layout per block (the last strip of a row may be kPadL wide); `ticket` and
+// `nscale` hold one entry per descriptor and 64-row block of a pack (block k
+// at index k nmats + descriptor), tickets zero between launches.
 constexpr int kPrepRows = 64;
 constexpr int kPrepCols = 256;
+// BF16 matrices with a short side <= 64 are packed, up to kMaxPack of one
+// shape, into one descriptor of kMaxPack 64-row blocks (block-diagonal A)
+constexpr int kMaxPack = 4;
 
 // sets the thread-local message returned by pe_last_error()
 void set_last_error(const char* msg);
@@ -40,13 +44,18 @@ typedef __nv_bfloat16 bf16;
 // (X) or s x s (A, B) padded row-major buffers with leading dimension Lp/sp.
 struct DevMat {
     void* user;          // caller's m x n buffer (in/out)
+    void* pack[kMaxPack - 1];  // pack: caller matrices 1 .. npack-1 of the same shape as `user`
+                         // (s <= 64), whose canonical rows are 64 k .. 64 k + 63 of this
+                         // descriptor's buffers (matrix 0 = `user` at rows 0 .. 63)
+    int32_t npack;       // matrices in the descriptor (0: a plain descriptor)
     int64_t ld;          // caller's leading dimension (elements)
     int32_t m, n;        // caller's shape
     int32_t trans;       // 1 when m > n: X = G^T
     int32_t io;          // pe_io_type of the caller's buffer
     int32_t s, L;        // logical short / long side
     int32_t sp, Lp;      // padded sizes (multiples of kPadS / kPadL)
-    int32_t part0, npart;  // range of this matrix's prepare tiles (norm partials)
+    int32_t part0, npart;  // prepare strips (norm partials) part0 .. part0 + npart; in a pack,
+                           // block k's strips follow at part0 + k npart
     int32_t out_tma;       // 1 when the caller's buffer admits TMA stores
     float* xf;           // FP32 X (master; updated in place on the BF16x3 path)
     float* xf2;          // FP32 ping-pong partner (FP32 path)
@@ -81,11 +90,18 @@ enum PrepOut { kPrepF32 = 1, kPrepBF16 = 2, kPrepBF16Lo = 4, kPrepCode = 8,
 // Final store of element (i, l) of the canonical result X_T: into the
 // caller's matrix, or for a fused Muon step W(i, l) <- W(i, l) - lr X_T(i, l).
 __device__ __forceinline__ void out_user(const DevMat& M, int i, int l, float v) {
+    void* user = M.user;
+    if (M.npack && i >= 64) {   // matrix i / 64 of a pack
+        const int k = i >> 6;
+        if (k >= M.npack) return;
+        user = M.pack[k - 1];
+        i -= 64 * k;
+    }
     if (i >= M.s || l >= M.L) return;
     const int64_t idx = M.trans ? (int64_t)l * M.ld + i : (int64_t)i * M.ld + l;
     if (M.w) M.w[idx] = __fadd_rn(M.w[idx], __fmul_rn(-M.lr, v));   // the rounding of a TMA reduce-add
-    else if (M.io == PE_IO_BF16) reinterpret_cast<bf16*>(M.user)[idx] = __float2bfloat16_rn(v);
-    else reinterpret_cast<float*>(M.user)[idx] = v;
+    else if (M.io == PE_IO_BF16) reinterpret_cast<bf16*>(user)[idx] = __float2bfloat16_rn(v);
+    else reinterpret_cast<float*>(user)[idx] = v;
 }
 
 // Compact master of X on the BF16 path: X is kept as hi = BF16 (the MMA

@@ -26,26 +26,28 @@ __device__ __forceinline__ float load_in(const void* base, int io, int64_t idx) 
     return reinterpret_cast<const float*>(base)[idx];
 }
 
-// four consecutive inputs of row `row` from column `col` (zero outside the matrix)
-__device__ __forceinline__ float4 load4(const DevMat& M, bool vec, int rows, int cols, int row, int col) {
+// four consecutive inputs of row `row` from column `col` of the caller's
+// matrix at `src` (zero outside the matrix)
+__device__ __forceinline__ float4 load4(const DevMat& M, const void* src, bool vec, int rows, int cols, int row,
+                                        int col) {
     float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
     if (row >= rows) return r;
     const int64_t base = (int64_t)row * M.ld + col;
     if (vec && col + 3 < cols) {
         if (M.io == PE_IO_BF16) {
-            const uint2 u = __ldcs(reinterpret_cast<const uint2*>(reinterpret_cast<const bf16*>(M.user) + base));
+            const uint2 u = __ldcs(reinterpret_cast<const uint2*>(reinterpret_cast<const bf16*>(src) + base));
             const __nv_bfloat162 p0 = *reinterpret_cast<const __nv_bfloat162*>(&u.x);
             const __nv_bfloat162 p1 = *reinterpret_cast<const __nv_bfloat162*>(&u.y);
             r = make_float4(__low2float(p0), __high2float(p0), __low2float(p1), __high2float(p1));
         } else {
-            r = __ldcs(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(M.user) + base));
+            r = __ldcs(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(src) + base));
         }
         return r;
     }
-    if (col + 0 < cols) r.x = load_in(M.user, M.io, base + 0);
-    if (col + 1 < cols) r.y = load_in(M.user, M.io, base + 1);
-    if (col + 2 < cols) r.z = load_in(M.user, M.io, base + 2);
-    if (col + 3 < cols) r.w = load_in(M.user, M.io, base + 3);
+    if (col + 0 < cols) r.x = load_in(src, M.io, base + 0);
+    if (col + 1 < cols) r.y = load_in(src, M.io, base + 1);
+    if (col + 2 < cols) r.z = load_in(src, M.io, base + 2);
+    if (col + 3 < cols) r.w = load_in(src, M.io, base + 3);
     return r;
 }
 
@@ -126,37 +128,43 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
     if (blockIdx.x == 0) {
         for (int i = threadIdx.x; i < ncounters; i += blockDim.x) counters[i] = 0;
     }
+    // canonical rows i0 .. i0 + 63 of the descriptor; in a pack they are
+    // rows r0s = i0 - 64 blk .. of the pack's matrix blk
+    const int blk = M.npack ? tk.tm : 0;
+    const void* src = (blk == 0) ? M.user : (blk < M.npack ? M.pack[blk - 1] : nullptr);
     const int i0 = tk.tm * kPrepRows, l0 = tk.tn * kPrepCols;
+    const int r0s = i0 - 64 * blk;
     const int tid = threadIdx.x;
     const int esz = (M.io == PE_IO_BF16) ? 2 : 4;
-    const bool vec = (reinterpret_cast<uintptr_t>(M.user) % (4 * esz) == 0) && (M.ld % 4 == 0) &&
+    const bool vec = (reinterpret_cast<uintptr_t>(src) % (4 * esz) == 0) && (M.ld % 4 == 0) &&
                      (!MUON || reinterpret_cast<uintptr_t>(M.mom) % 16 == 0);
     const bool mom_store = !(outputs & kPrepNoMom);
     float ss = 0.f;
     // all sixteen loads of a thread are issued before any store (the
     // compiler cannot move loads of G across stores that may alias it)
     float4 ld[16];
-    if ((outputs & kPrepSkipPad) && i0 >= M.s) {
-        // every row of the strip is padding: the workspace holds zeros there
-        // from the plan's creation on, and no step ever writes anything else
+    if (!src || ((outputs & kPrepSkipPad) && r0s >= M.s)) {
+        // every row of the strip is padding (or an empty block of a pack): the
+        // workspace holds zeros there from the plan's creation on, and no step
+        // ever writes anything else
     } else if (!M.trans) {
         // X[i][l] = G[i][l]; G is s x L. 64 threads per row, 4 rows per pass.
         const int c = (tid & 63) * 4, r0 = tid >> 6;
         const bool on = l0 + c < M.Lp;   // the last strip of a row may be 128 wide
         // interior strip of an FP32 matrix: sixteen unconditional vector loads
-        const bool interior = vec && M.io != PE_IO_BF16 && i0 + kPrepRows <= M.s && l0 + kPrepCols <= M.L;
+        const bool interior = vec && M.io != PE_IO_BF16 && r0s + kPrepRows <= M.s && l0 + kPrepCols <= M.L;
         if (interior) {
-            const float* g = reinterpret_cast<const float*>(M.user) + (int64_t)(i0 + r0) * M.ld + l0 + c;
+            const float* g = reinterpret_cast<const float*>(src) + (int64_t)(r0s + r0) * M.ld + l0 + c;
 #pragma unroll
             for (int p = 0; p < 16; ++p) ld[p] = __ldcs(reinterpret_cast<const float4*>(g + (int64_t)4 * p * M.ld));
         } else {
 #pragma unroll
             for (int p = 0; p < 16; ++p)
-                ld[p] = on ? load4(M, vec, M.s, M.L, i0 + r0 + 4 * p, l0 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                ld[p] = on ? load4(M, src, vec, M.s, M.L, r0s + r0 + 4 * p, l0 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         if (MUON && on) {
 #pragma unroll
-            for (int p = 0; p < 16; ++p) ld[p] = momentum4(M, vec, M.s, M.L, i0 + r0 + 4 * p, l0 + c, ld[p], mom_store);
+            for (int p = 0; p < 16; ++p) ld[p] = momentum4(M, vec, M.s, M.L, r0s + r0 + 4 * p, l0 + c, ld[p], mom_store);
         }
         if (on) {
 #pragma unroll
@@ -170,23 +178,23 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
         // X[i][l] = G[l][i]; G is L x s: read G rows l with i contiguous (16
         // threads per 64-float row segment), transpose 64 x 64 sub-tiles in smem
         const int rr = tid >> 4, c4 = (tid & 15) * 4;
-        const bool interior = vec && M.io != PE_IO_BF16 && l0 + kPrepCols <= M.L && i0 + kPrepRows <= M.s;
+        const bool interior = vec && M.io != PE_IO_BF16 && l0 + kPrepCols <= M.L && r0s + kPrepRows <= M.s;
         if (interior) {
-            const float* g = reinterpret_cast<const float*>(M.user) + (int64_t)(l0 + rr) * M.ld + i0 + c4;
+            const float* g = reinterpret_cast<const float*>(src) + (int64_t)(l0 + rr) * M.ld + r0s + c4;
 #pragma unroll
             for (int p = 0; p < 16; ++p) ld[p] = __ldcs(reinterpret_cast<const float4*>(g + (int64_t)16 * p * M.ld));
         } else {
 #pragma unroll
             for (int p = 0; p < 16; ++p) {
                 const int l = l0 + rr + 16 * p;   // sub-tile p / 4, row rr + 16 (p % 4)
-                ld[p] = (l < M.Lp) ? load4(M, vec, M.L, M.s, l, i0 + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                ld[p] = (l < M.Lp) ? load4(M, src, vec, M.L, M.s, l, r0s + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
         if (MUON) {
 #pragma unroll
             for (int p = 0; p < 16; ++p) {
                 const int l = l0 + rr + 16 * p;
-                if (l < M.Lp) ld[p] = momentum4(M, vec, M.L, M.s, l, i0 + c4, ld[p], mom_store);
+                if (l < M.Lp) ld[p] = momentum4(M, vec, M.L, M.s, l, r0s + c4, ld[p], mom_store);
             }
         }
 #pragma unroll
@@ -222,7 +230,7 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
         for (int w = 0; w < 8; ++w) s += red[w];
         partials[blockIdx.x] = s;
         __threadfence();
-        const unsigned t = atomicAdd(&ticket[tk.mat], 1u);
+        const unsigned t = atomicAdd(&ticket[blk * nmats + tk.mat], 1u);
         s_last = (t == (unsigned)M.npart - 1);
     }
     __syncthreads();
@@ -232,9 +240,10 @@ __global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__
     // butterfly), and the ticket reset for the next launch
     __threadfence();
     if (tid < 32) {
-        const int lane = tid, m = tk.mat;
+        const int lane = tid, m = blk * nmats + tk.mat;
+        const int p0 = M.part0 + blk * M.npart;
         double s = 0.0;
-        for (int i = lane; i < M.npart; i += 32) s += *((volatile double*)&partials[M.part0 + i]);
+        for (int i = lane; i < M.npart; i += 32) s += *((volatile double*)&partials[p0 + i]);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
             const double nu = sqrt(s);

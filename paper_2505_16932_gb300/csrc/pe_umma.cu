@@ -83,6 +83,7 @@ struct StepArgs {
     float a, b, c;
     int step, cur, last, dependent, withhold;
     int cubic;          // c = 0 in every step: the Gram epilogue writes B = b A, no square tiles
+    int nmats;          // descriptors (block k of a pack has nscale[k nmats + mat])
     uint64_t wait_ns;
     long long* prof;    // optional per-CTA cycle counters (debug)
     const float* nscale;  // per-matrix normalisation factor, applied in step 0
@@ -936,7 +937,8 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             const bool needs_in = (g.kind != kGram);
             // step 0 runs on the unscaled prepared X and applies the
             // normalisation factor s: A = s^2 X X^T, X_1 = s (a X + B X)
-            const float s0 = (A.step == 0) ? A.nscale[g.mat] : 1.f;
+            // (a warp's 32 rows lie in one 64-row block of a pack)
+            const float s0 = (A.step == 0) ? A.nscale[(M.npack ? (gi0 >> 6) : 0) * A.nmats + g.mat] : 1.f;
             if (g.kind == kSquare && A.dependent) {   // A (FP32) comes from other CTAs
                 const long long c0 = clock64();
                 if (NS == 1) {
@@ -996,6 +998,9 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                 const int col0 = cb + i * 32;
                 const int cls = sym ? chunk_class(gi0, col0) : kChunkUpper;
                 if (cls == kChunkLower) continue;
+                // pack: the Gram's blocks between different matrices stay zero
+                // (never stored; the square then computes zeros there)
+                if (g.kind == kGram && M.npack && (gi0 >> 6) != (col0 >> 6)) continue;
                 // next stored chunk (for the prefetch)
                 int nx = i + 1;
                 if (sym)
@@ -1514,7 +1519,7 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
         const int esz = (M.io == PE_IO_BF16) ? 2 : 4;
         M.out_tma = 0;
         void* out = M.w ? (void*)M.w : M.user;   // fused Muon step: the box is reduce-added into W
-        if (P->nsplit == 1 && reinterpret_cast<uintptr_t>(out) % 16 == 0 && (M.ld * esz) % 16 == 0) {
+        if (P->nsplit == 1 && !M.npack && reinterpret_cast<uintptr_t>(out) % 16 == 0 && (M.ld * esz) % 16 == 0) {
             M.out_tma = make_map(enc, mp + kMapEOut, out, M.m, M.n, M.ld * esz, 32, 32, esz == 4 ? F32 : BF,
                                  esz == 4 ? S128 : S64)
                             ? 1
@@ -1689,6 +1694,7 @@ cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, i
     A.last = last;
     A.withhold = withhold;
     A.cubic = P->cubic ? 1 : 0;
+    A.nmats = P->count;
     A.wait_ns = wait_ns;
     A.prof = reinterpret_cast<long long*>(P->prof);
     *launched = 0;

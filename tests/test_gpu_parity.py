@@ -387,3 +387,36 @@ def test_host_buffers_equal_device_call(ngroups, pinned):
     pe.pe_sync_status()
     for h, X in zip(H_out, Xs):
         assert torch.equal(h, X.cpu())
+
+
+# ------------------------------------------- pairs of small matrices (BF16)
+
+def test_small_matrix_packs_bitwise_equal_unpacked():
+    """BF16 matrices with a short side <= 64 of one shape share descriptors of
+    four 64-row blocks (block-diagonal Gram). Each matrix's Gram, square and
+    update see the same products in the same order as alone, so the result
+    equals the unpacked plan's bit for bit; covers both orientations, a full
+    pack plus a pack of one (5 matrices), packs of 2 and 3, a ragged long
+    side, a shape seen once (not packed) and a large matrix."""
+    shapes = ([(768, 64)] * 5 + [(40, 500)] * 2 + [(64, 64)] * 3 + [(20, 33)] + [(256, 300)])
+    # log-spaced spectra in [1e-3, 1] (the heavy-tailed class; iid Gaussian
+    # inputs are the well-conditioned class of the BF16 limit above)
+    mats = [synth.random_svd_case(seed=23 + i, m=m, n=n, lo=1e-3).G for i, (m, n) in enumerate(shapes)]
+    tab = table(1e-3, 5)
+    outs = []
+    try:
+        for nopair in (0, 1):
+            pe.pe_debug_set(9, nopair)
+            pe.pe_release()
+            Xs = [to_dev(G) for G in mats]
+            pe.pe_polar_batched(Xs, tab, "bf16")
+            pe.pe_sync_status()
+            outs.append([X.cpu() for X in Xs])
+    finally:
+        pe.pe_debug_set(9, 0)
+        pe.pe_release()
+    for a, b, sh in zip(outs[0], outs[1], shapes):
+        assert torch.equal(a, b), sh
+    for X, G in zip(outs[0], mats):
+        ref = O.polar_express(G.astype(np.float32).astype(np.float64), tab)
+        assert O.rel_fro(X.numpy().astype(np.float64), ref) <= BF16_TOL
