@@ -455,6 +455,9 @@ def main():
         if not args.no_extras:
             extras = accuracy_and_fp32(pe, torch, wl, table, dev_in, dtype, flush, stream, args, refs)
             extras["newton_schulz5"] = newton_schulz_line(pe, torch, wl, dev_in, dtype, flush, stream, refs, args)
+            if dtype == "bf16":
+                extras["torch_cublas_bf16"] = cublas_listing_line(torch, wl, table, dev_in, flush, stream, refs,
+                                                                  ms_per_step, args)
         if args.sweep or wl.name == "ill_conditioned":
             extras["error_vs_T"] = error_sweep(pe, torch, wl, dev_in, flush, stream)
         if not args.no_largest and wl.name != "large_dense" and world == 1:
@@ -477,6 +480,7 @@ def main():
                    "input_bytes": in_bytes, "l2": "inputs larger than L2 and a 258 MB L2 flush before each step",
                    "note": wl.note},
         "us_per_muon_step": 1e3 * ms_per_step,
+        "us_per_muon_step_median": 1e3 * statistics.median(step_ms),
         "us_per_poly_step": 1e3 * ms_per_step / T,
         "wall_s_timed": wall,
         "gpu_launches": int(launches),
@@ -608,6 +612,68 @@ def newton_schulz_line(pe, torch, wl, dev_in, dtype, flush, stream, refs, args):
     return {"value": algorithmic_flops(wl.shapes, wl.T) / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
             "T": wl.T, "dtype": dtype, "max_sigma_err_sample": max(errs) if errs else None,
             "polar_express_fp64_max_sigma_err_sample": max(pe_errs) if pe_errs else None}
+
+
+def cublas_listing_line(torch, wl, table, dev_in, flush, stream, refs, ours_ms, args):
+    """The same method written with PyTorch library calls (cuBLAS GEMMs), the
+    form of the paper's own online code (App. A): X, A and B stored in BF16,
+    one batched GEMM call per product for each stack of same-shape matrices,
+    the combinations b A + c A A and a X + B X folded into the GEMM calls
+    (baddbmm's beta and alpha), the whole step sequence replayed from a CUDA
+    graph. A comparison point for the kernels of this library, which it
+    does not call; time per Muon step and relative error on the accuracy
+    sample against the FP64 iteration."""
+    groups = {}
+    for i, sh in enumerate(wl.shapes):
+        groups.setdefault(sh, []).append(i)
+    stacks = [(sh, idx, torch.stack([dev_in[i] for i in idx])) for sh, idx in groups.items()]
+    outs = [torch.empty_like(G) for _, _, G in stacks]
+    coef = [tuple(float(v) for v in row) for row in table]
+
+    def step_sequence():
+        for (sh, _, G), out in zip(stacks, outs):
+            nrm = torch.linalg.vector_norm(G, dim=(1, 2), keepdim=True)
+            X = (G / (1.01 * nrm + 1e-7)).to(torch.bfloat16)
+            if sh[0] > sh[1]:
+                X = X.mT                               # short side first
+            for a, b, c in coef:
+                A = torch.bmm(X, X.mT)
+                B = torch.baddbmm(A, A, A, beta=b, alpha=c)
+                X = torch.baddbmm(X, B, X, beta=a, alpha=1.0)
+            out.copy_(X.mT if sh[0] > sh[1] else X)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step_sequence()
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step_sequence()
+    graph.replay()
+    n = max(3, min(20, args.steps // 5))
+    tot = 0.0
+    for _ in range(n):
+        flush.fill_(3.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        graph.replay()
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    ms = tot / n
+    errs = []
+    for (sh, idx, _), out in zip(stacks, outs):
+        for k, i in enumerate(idx):
+            if i in refs:
+                errs.append(_rel_fro(out[k].cpu().numpy().astype(np.float64), refs[i][0]))
+    del graph, stacks, outs
+    torch.cuda.empty_cache()
+    return {"value": algorithmic_flops(wl.shapes, wl.T) / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
+            "T": wl.T, "kind": "torch bmm/baddbmm (cuBLAS) in BF16 per same-shape stack, CUDA graph",
+            "rel_fro_vs_fp64_iteration_sample_max": max(errs) if errs else None,
+            "speedup_of_this_library": ms / ours_ms}
 
 
 def error_sweep(pe, torch, wl, dev_in, flush, stream, Ts=(2, 4, 6, 8, 10, 12), gamma=1e-3):
