@@ -16,13 +16,16 @@ Contents
               short side (Alg. 1, Sec. 3.5 Horner form), its spectral form
               U p(S) V^T (App. C), polar via SVD (Eq. matrixsign) and the error
               metrics.
+``spectrum_init`` the spectrum-aware initialisation of App. H (k = 1): power
+              method lower bound z of sigma_1, the cubic of Eq. init_poly, and
+              the table that puts it before the Polar Express steps.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against facts fixed by
 the paper or by mathematics (printed table, equioscillation, closed forms,
 invariants, library routines, brute force). The one claim left unpinned is the
 ``p(x)/x >= 0.236`` remark of App. G, which the oracle does not implement.
 """
-from . import minimax, iteration  # noqa: F401
+from . import minimax, iteration, spectrum_init  # noqa: F401
 from .minimax import (  # noqa: F401
     KAPPA,
     NoConvergence,
