@@ -458,6 +458,7 @@ def main():
             if dtype == "bf16":
                 extras["torch_cublas_bf16"] = cublas_listing_line(torch, wl, table, dev_in, flush, stream, refs,
                                                                   ms_per_step, args)
+            extras["spectrum_bound"] = spectrum_bound_line(pe, wl, dev_in)
         if args.sweep or wl.name == "ill_conditioned":
             extras["error_vs_T"] = error_sweep(pe, torch, wl, dev_in, flush, stream)
         if not args.no_largest and wl.name != "large_dense" and world == 1:
@@ -674,6 +675,24 @@ def cublas_listing_line(torch, wl, table, dev_in, flush, stream, refs, ours_ms, 
             "T": wl.T, "kind": "torch bmm/baddbmm (cuBLAS) in BF16 per same-shape stack, CUDA graph",
             "rel_fro_vs_fp64_iteration_sample_max": max(errs) if errs else None,
             "speedup_of_this_library": ms / ours_ms}
+
+
+def spectrum_bound_line(pe, wl, dev_in, iters=10):
+    """Cost of the App. H bound (the power method, ``iters`` steps, on G) for
+    one matrix of each distinct shape: host wall time of the blocking call
+    (its buffers, about five launches per step and the read-back of z), and
+    z / f, which decides whether the cubic applies (z / f > 1 / sqrt 2)."""
+    seen = {}
+    for i, sh in enumerate(wl.shapes):
+        seen.setdefault(sh, i)
+    rows = []
+    for sh, i in list(seen.items())[:4]:
+        v0 = np.random.default_rng(i).standard_normal(min(sh)).astype(np.float32)
+        pe.pe_spectrum_bound(dev_in[i], v0, iters)
+        t0 = time.perf_counter()
+        z, f = pe.pe_spectrum_bound(dev_in[i], v0, iters)
+        rows.append({"shape": list(sh), "ms": 1e3 * (time.perf_counter() - t0), "z_over_f": z / f if f else None})
+    return {"iters": iters, "rows": rows}
 
 
 def error_sweep(pe, torch, wl, dev_in, flush, stream, Ts=(2, 4, 6, 8, 10, 12), gamma=1e-3):

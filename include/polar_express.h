@@ -386,6 +386,48 @@ int pe_split_step(pe_split_t handle, int t, const float* A, int64_t lda);
 /* Frees the handle's workspace (after the stream's work has finished). */
 int pe_split_close(pe_split_t handle);
 
+/* ------------------------------------ spectrum-aware initialisation
+ *
+ * For matrices with one dominant singular value (App. H, the case k = 1).
+ * With X_0 = G / (1.01 ||G||_F + 1e-7) on the short side (as pe_polar
+ * normalises) and f = ||X_0||_F: the power method (subspace iteration with
+ * one vector) on X_0 X_0^T gives z <= sigma_1(X_0); the Frobenius identity
+ * then bounds sigma_1 in [z, f] and every other singular value by
+ * w = sqrt(f^2 - z^2). When 2 z^2 > f^2 the odd cubic p(x) = a x + b x^3 with
+ * p(w) = p(z) = 1 (Eq. init_poly, as a polynomial of x / f) maps the spectrum
+ * into [l', 1], l' = min(l / w, p(f)), and T Polar Express steps for [l', 1]
+ * follow; otherwise T + 1 ordinary steps for [l, 1].
+ */
+
+/* Lower bound of sigma_1 by `iters` power steps v <- X_0 X_0^T v / ||.||
+ * from v0, then z = ||X_0^T v||.
+ *   X      device, m x n row-major contiguous FP32 (ld = n); read only.
+ *   v0     host, min(m, n) floats, nonzero and finite (the method's random
+ *          start, drawn by the caller).
+ *   iters  0..10000.
+ *   z, f   host out: the bound z and f = ||X_0||_F (both 0 for G = 0).
+ * Synchronises `stream` (the bound is needed on the host). Device buffers
+ * are allocated and freed per call. Errors: PE_EINVAL, PE_ECUDA. */
+int pe_spectrum_bound(const void* X, int64_t m, int64_t n, const float* v0, int iters, double* z, double* f,
+                      void* stream);
+
+/* Host: the coefficient table of the initialised iteration, T + 1 rows of
+ * (a, b, c) into table (caller-owned, 3 (T + 1) doubles): row 0 the cubic
+ * (a, b, 0) and rows 1..T the pe_coeffs(5, l', T, 1.01) composition, or, when
+ * the cubic does not apply, pe_coeffs(5, l, T + 1, 1.01). z is shrunk by a
+ * relative 1e-5 first (so that an FP32 evaluation of the bound cannot exceed
+ * sigma_1 by rounding). info (nullable, 6 doubles): applied (1 or 0), the z
+ * used, f, a, b, l'. T in 0..63, l in (0, 1]. Errors: PE_EINVAL, PE_ENOCONV. */
+int pe_spectrum_aware_table(double z, double f, double l, int T, double* table, double* info);
+
+/* pe_spectrum_bound, pe_spectrum_aware_table, then pe_polar with that table
+ * (T + 1 steps) on X in place. X as for pe_polar (FP32, device, in/out);
+ * dtype PE_FP32, PE_BF16 or PE_BF16X3; info as for pe_spectrum_aware_table.
+ * Each call builds a plan for its data-dependent table (a cached tuned
+ * schedule of the same shape is reused). Errors: as the three calls. */
+int pe_polar_spectrum_aware(void* X, int64_t m, int64_t n, double l, int T, int dtype, const float* v0, int iters,
+                            double* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -90,6 +90,10 @@ def lib() -> ctypes.CDLL:
         "pe_split_gram": (c_i, [c_p, c_i, c_p, c_i64]),
         "pe_split_step": (c_i, [c_p, c_i, c_p, c_i64]),
         "pe_split_close": (c_i, [c_p]),
+        "pe_spectrum_bound": (c_i, [c_p, c_i64, c_i64, ctypes.POINTER(ctypes.c_float), c_i, P_d, P_d, c_p]),
+        "pe_spectrum_aware_table": (c_i, [c_d, c_d, c_d, c_i, P_d, P_d]),
+        "pe_polar_spectrum_aware": (c_i, [c_p, c_i64, c_i64, c_d, c_i, c_i, ctypes.POINTER(ctypes.c_float), c_i,
+                                          P_d, c_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -179,6 +183,60 @@ def pe_polar(X, table, dtype: str = "bf16", stream=None, norm_scale: float = 1.0
                              ctypes.c_void_p(_stream_handle(stream)))
     _check(code)
     return X
+
+
+def _fp32_matrix(X):
+    import torch
+    _check_tensor(X)
+    if X.dtype != torch.float32 or not X.is_contiguous():
+        raise PolarExpressError(PE_EINVAL, "X must be a contiguous float32 CUDA matrix")
+
+
+def _start_vector(X, v0) -> np.ndarray:
+    v = np.ascontiguousarray(np.asarray(v0, dtype=np.float32).reshape(-1))
+    if v.shape[0] != min(X.shape[0], X.shape[1]):
+        raise PolarExpressError(PE_EINVAL, "v0 must have min(m, n) entries")
+    return v
+
+
+_SA_KEYS = ("applied", "z", "f", "a", "b", "l_after")
+
+
+def pe_spectrum_bound(X, v0, iters: int = 10, stream=None):
+    """(z, f) of the spectrum-aware initialisation (App. H): z <= sigma_1 of
+    the normalised X by ``iters`` power steps from the start vector v0
+    (min(m, n) floats), f its Frobenius norm. Synchronises ``stream``."""
+    _fp32_matrix(X)
+    v = _start_vector(X, v0)
+    z, f = ctypes.c_double(), ctypes.c_double()
+    _check(lib().pe_spectrum_bound(ctypes.c_void_p(X.data_ptr()), X.shape[0], X.shape[1],
+                                   v.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), int(iters),
+                                   ctypes.byref(z), ctypes.byref(f), ctypes.c_void_p(_stream_handle(stream))))
+    return z.value, f.value
+
+
+def pe_spectrum_aware_table(z: float, f: float, l: float, T: int):
+    """(table (T + 1, 3), info) of the initialised iteration (host)."""
+    tab = np.zeros((T + 1, 3))
+    info = np.zeros(6)
+    _check(lib().pe_spectrum_aware_table(float(z), float(f), float(l), int(T), _dptr(tab), _dptr(info)))
+    d = dict(zip(_SA_KEYS, info.tolist()))
+    d["applied"] = bool(d["applied"])
+    return tab, d
+
+
+def pe_polar_spectrum_aware(X, l: float, T: int, v0, dtype: str = "bf16", iters: int = 10, stream=None):
+    """In place on a contiguous float32 CUDA matrix: the App. H cubic (when it
+    applies) and T Polar Express steps; returns the info dict."""
+    _fp32_matrix(X)
+    v = _start_vector(X, v0)
+    info = np.zeros(6)
+    _check(lib().pe_polar_spectrum_aware(ctypes.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], float(l), int(T),
+                                         DTYPES[dtype], v.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                         int(iters), _dptr(info), ctypes.c_void_p(_stream_handle(stream))))
+    d = dict(zip(_SA_KEYS, info.tolist()))
+    d["applied"] = bool(d["applied"])
+    return d
 
 
 def pe_polar_batched(Xs: Sequence, table, dtype: str = "bf16", stream=None, flags: int = 0,

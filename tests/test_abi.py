@@ -133,3 +133,46 @@ def test_host_entry_argument_errors_without_gpu(L):
     assert L.pe_polar_batched_host(ptrs, ptrs, ms, ms, 0, tp, 5, pe.PE_BF16, 0, None) == pe.PE_EINVAL
     fake = (ctypes.c_void_p * 1)(0x10000)
     assert L.pe_polar_batched_host(fake, fake, ms, ms, 1, tp, 5, pe.PE_BF16, -1, None) == pe.PE_EINVAL
+
+
+def test_spectrum_entry_argument_errors_without_gpu(L):
+    F = ctypes.POINTER(ctypes.c_float)
+    v = np.ones(4, dtype=np.float32)
+    vz = np.zeros(4, dtype=np.float32)
+    z, f = ctypes.c_double(), ctypes.c_double()
+    fake = ctypes.c_void_p(0x10000)
+    args = lambda X, m, n, vv, it: (X, m, n, vv.ctypes.data_as(F), it, ctypes.byref(z), ctypes.byref(f), None)  # noqa: E731
+    assert L.pe_spectrum_bound(*args(None, 4, 8, v, 5)) == pe.PE_EINVAL
+    assert L.pe_spectrum_bound(*args(fake, 0, 8, v, 5)) == pe.PE_EINVAL
+    assert L.pe_spectrum_bound(*args(fake, 4, 8, v, -1)) == pe.PE_EINVAL
+    assert L.pe_spectrum_bound(*args(fake, 4, 8, vz, 5)) == pe.PE_EINVAL
+    assert b"nonzero" in L.pe_last_error()
+    assert L.pe_spectrum_bound(*args(ctypes.c_void_p(0x10002), 4, 8, v, 5)) == pe.PE_EINVAL
+    info = np.zeros(6)
+    P = ctypes.POINTER(ctypes.c_double)
+    assert L.pe_polar_spectrum_aware(fake, 4, 8, 1e-3, 5, 7, v.ctypes.data_as(F), 5, info.ctypes.data_as(P),
+                                     None) == pe.PE_EINVAL
+    assert L.pe_polar_spectrum_aware(fake, 4, 8, 0.0, 5, pe.PE_BF16, v.ctypes.data_as(F), 5,
+                                     info.ctypes.data_as(P), None) == pe.PE_EINVAL
+    tab = np.zeros((6, 3))
+    assert L.pe_spectrum_aware_table(0.9, 1.0, 1e-3, -1, tab.ctypes.data_as(P), None) == pe.PE_EINVAL
+    assert L.pe_spectrum_aware_table(0.9, 1.0, 2.0, 5, tab.ctypes.data_as(P), None) == pe.PE_EINVAL
+    assert L.pe_spectrum_aware_table(float("nan"), 1.0, 1e-3, 5, tab.ctypes.data_as(P), None) == pe.PE_EINVAL
+
+
+@pytest.mark.parametrize("z,f,l,T", [(0.95, 0.99, 1e-3, 5), (0.999, 0.99999, 1e-7, 8), (0.72, 1.0, 1e-4, 3),
+                                     (0.5, 0.99, 1e-3, 5), (0.7, 0.99, 1e-3, 4), (0.9, 1.0, 1e-3, 0),
+                                     (0.0, 0.0, 1e-3, 5)])
+def test_spectrum_aware_table_matches_oracle(L, z, f, l, T):
+    """Host table of the App. H initialisation against the oracle's: the cubic
+    row to rounding, the following composition from the same l'."""
+    from oracle import spectrum_init as S
+    tab, info = pe.pe_spectrum_aware_table(z, f, l, T)
+    ref, rinfo = S.spectrum_aware_table(z, f, l, T)
+    assert info["applied"] == rinfo["applied"]
+    assert tab.shape == (T + 1, 3) and len(ref) == T + 1
+    assert np.allclose(tab, np.array(ref), rtol=1e-12, atol=0)
+    assert math.isclose(info["l_after"], rinfo["l_after"], rel_tol=1e-14)
+    if info["applied"]:
+        assert tab[0, 2] == 0.0
+        assert math.isclose(info["a"], rinfo["a"], rel_tol=1e-14) and math.isclose(info["b"], rinfo["b"], rel_tol=1e-14)
