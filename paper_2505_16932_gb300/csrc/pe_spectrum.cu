@@ -8,7 +8,9 @@
 //      singular value <= w = sqrt(f^2 - z^2); when the intervals are disjoint
 //      the odd cubic p(x) = a x + b x^3 with p(w) = p(z) = 1 (Eq. init_poly,
 //      written for f = 1; here that polynomial of x / f) maps the spectrum
-//      into [min(l / w, p(f)), 1], and Polar Express continues from there.
+//      into [min(l / w, p(f)), 1], and Polar Express continues from there,
+//      if that composition's final greedy bound beats the plain one with one
+//      more step (the cubic pays off when z is close to f).
 // The power method is memory-bound matrix-vector work on G itself (two
 // passes per iteration); its kernels are plain coalesced FP32 streams with
 // deterministic reductions (fixed summation order, FP64 norms).
@@ -285,21 +287,37 @@ int pe_spectrum_aware_table(double z, double f, double l, int T, double* table, 
     if (!std::isfinite(z) || !std::isfinite(f) || z < 0.0 || f < 0.0) return sfail(PE_EINVAL, "bad z or f");
     const double zs = z * (1.0 - kZSafety);
     double a = 0.0, b = 0.0, w = 0.0;
-    const bool applied = init_cubic(zs, f, &a, &b, &w);
-    double lp = l;
     const char* why = nullptr;
-    int r;
+    // the plain composition with one more step, and its greedy bound after the last step
+    std::vector<double> plain(3 * (T + 1)), pbounds(2 * (T + 2));
+    int r = coeffs_table(5, l, T + 1, 1.01, -1.0, 0u, plain.data(), pbounds.data(), nullptr, &why);
+    if (r != PE_OK) return sfail(r, why ? why : "coefficient solve failed");
+    bool applied = init_cubic(zs, f, &a, &b, &w);
+    double lp = l;
     if (applied) {
+        // the cubic, then the composition for [l', 1]; kept only if its final
+        // greedy bound beats the plain one (the cubic pays off when z is near f)
         const double pf = f * (a + b * f * f);
         lp = std::min(l / w, pf);
-        table[0] = a;
-        table[1] = b;
-        table[2] = 0.0;
-        r = T > 0 ? coeffs_table(5, lp, T, 1.01, -1.0, 0u, table + 3, nullptr, nullptr, &why) : PE_OK;
-    } else {
-        r = coeffs_table(5, l, T + 1, 1.01, -1.0, 0u, table, nullptr, nullptr, &why);
+        double l_final = lp;
+        std::vector<double> rest(3 * std::max(T, 1)), rbounds(2 * (T + 1));
+        if (T > 0) {
+            r = coeffs_table(5, lp, T, 1.01, -1.0, 0u, rest.data(), rbounds.data(), nullptr, &why);
+            if (r != PE_OK) return sfail(r, why ? why : "coefficient solve failed");
+            l_final = rbounds[2 * T];
+        }
+        applied = l_final > pbounds[2 * (T + 1)];
+        if (applied) {
+            table[0] = a;
+            table[1] = b;
+            table[2] = 0.0;
+            for (int k = 0; k < 3 * T; ++k) table[3 + k] = rest[k];
+        }
     }
-    if (r != PE_OK) return sfail(r, why ? why : "coefficient solve failed");
+    if (!applied) {
+        lp = l;
+        for (int k = 0; k < 3 * (T + 1); ++k) table[k] = plain[k];
+    }
     if (info) {
         info[0] = applied ? 1.0 : 0.0;
         info[1] = zs;

@@ -88,17 +88,42 @@ def test_cubic_step_is_the_scalar_map_on_singular_values():
     U, V = _haar(rng, n), _haar(rng, n)
     s = np.concatenate([[1.0], np.geomspace(0.3, 1e-4, n - 1)])
     G = (U * s) @ V.T
-    X, table, info = S.spectrum_aware_polar(G, 1e-4, 0, rng.standard_normal(n), 10)
-    assert info["applied"] and len(table) == 1
-    a, b, _ = table[0]
+    X0, _ = O.normalise(G)
+    f = float(np.linalg.norm(X0))
+    z = S.power_bound(X0.T, rng.standard_normal(n), 10)
+    a, b, w = S.init_cubic(z, f)
+    X = O.polar_express(G, [(a, b, 0.0)])
     x = s / (1.01 * np.linalg.norm(s) + 1e-7)
     ref = (U * (a * x + b * x ** 3)) @ V.T
     assert np.max(np.abs(X - ref)) <= 1e-13
     # the mapped spectrum: at most 1, and each value at least min(x / w, p(f))
     px = a * x + b * x ** 3
+    pf = a * f + b * f ** 3
     assert px.max() <= 1 + 1e-12
-    assert np.all(px >= np.minimum(x / info["w"], info["p_f"]) * (1 - 1e-12))
-    assert info["l_after"] == min(1e-4 / info["w"], info["p_f"])
+    assert np.all(px >= np.minimum(x / w, pf) * (1 - 1e-12))
+
+
+def test_cubic_kept_only_when_its_final_bound_is_better():
+    """Spectra 1/i (the GPT-2-like workload): the intervals are disjoint but
+    the tail gains only f / w ~ 1.6, less than a quintic step, so the plain
+    composition is kept, and it is indeed the more accurate one; a gap of
+    100 (sigma_2 = 0.01) keeps the cubic, which is then the more accurate."""
+    for tail, keep in ((None, False), ((0.01, 1e-4), True)):
+        k = 768
+        s = 1.0 / np.arange(1, k + 1) if tail is None else np.concatenate([[1.0], np.geomspace(*tail, k - 1)])
+        x = s / (1.01 * np.linalg.norm(s) + 1e-7)
+        f, z = float(np.linalg.norm(x)), float(x.max())
+        assert 2 * z * z > f * f
+        table, info = S.spectrum_aware_table(z, f, 1e-4, 4)
+        assert info["applied"] == keep
+        plain, _ = O.optimal_composition(1e-4, 5, safety=1.01)
+        a, b, w = S.init_cubic(z * (1 - S.Z_SAFETY), f)
+        forced = [(a, b, 0.0)] + [tuple(r) for r in O.optimal_composition(min(1e-4 / w, a * f + b * f ** 3), 4,
+                                                                           safety=1.01)[0]]
+        e_plain = np.max(np.abs(O.compose_scalar(x, plain) - 1))
+        e_forced = np.max(np.abs(O.compose_scalar(x, forced) - 1))
+        assert (e_forced < e_plain) == keep, (e_forced, e_plain)
+        assert np.allclose(np.array(table), np.array(forced if keep else plain), rtol=0, atol=0)
 
 
 def test_no_cubic_without_a_dominant_singular_value():
