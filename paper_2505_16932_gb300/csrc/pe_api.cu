@@ -546,7 +546,6 @@ int autotune(Plan* P, cudaStream_t st) {
     PE_CU(cudaEventCreate(&a));
     PE_CU(cudaEventCreate(&b));
     PE_CU(cudaStreamSynchronize(st));
-    float best = 1e30f;
     int best_order = P->umma.order, best_mode = P->umma.mode;
     int r = PE_OK;
     const int n_orders = (P->key.count >= 8) ? 5 : 2;   // lagged interleaves need several matrices
@@ -557,26 +556,31 @@ int autotune(Plan* P, cudaStream_t st) {
         if (P->umma.max_clusters > 0) modes.push_back(1);
         if (P->umma.max_clusters2 > 0) modes.push_back(2);
     }
-    for (int cand = 0; cand < n_orders * (int)modes.size() && r == PE_OK; ++cand) {
-        const int order = cand % n_orders;
-        P->umma.mode = modes[cand / n_orders];
-        r = umma_schedule(&P->umma, order, &g_err);
-        if (r != PE_OK) break;
-        float ms = 1e30f;
-        for (int rep = 0; rep < 3 && r == PE_OK; ++rep) {   // warm-up, then the faster of two timed runs
+    // Round robin over the candidates (a warm-up pass, then two timed passes,
+    // the faster run of each candidate counts), so that a drift of clocks or
+    // power during tuning does not favour the candidates timed first.
+    const int ncand = n_orders * (int)modes.size();
+    std::vector<float> cand_ms(ncand, 1e30f);
+    for (int pass = 0; pass < 3 && r == PE_OK; ++pass) {
+        for (int cand = 0; cand < ncand && r == PE_OK; ++cand) {
+            P->umma.mode = modes[cand / n_orders];
+            r = umma_schedule(&P->umma, cand % n_orders, &g_err);
+            if (r != PE_OK) break;
             cudaEventRecord(a, st);
             r = enqueue(P, st, true);
             cudaEventRecord(b, st);
             if (cudaEventSynchronize(b) != cudaSuccess) r = cuda_fail(cudaGetLastError(), "autotune");
             float t = 0.f;
             cudaEventElapsedTime(&t, a, b);
-            if (rep > 0 && t < ms) ms = t;
+            if (pass > 0 && t < cand_ms[cand]) cand_ms[cand] = t;
         }
-        if (r == PE_OK && ms < best) {
-            best = ms;
-            best_order = order;
-            best_mode = P->umma.mode;
-        }
+    }
+    if (r == PE_OK) {
+        int bc = 0;
+        for (int cand = 1; cand < ncand; ++cand)
+            if (cand_ms[cand] < cand_ms[bc]) bc = cand;
+        best_mode = modes[bc / n_orders];
+        best_order = bc % n_orders;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
