@@ -226,10 +226,8 @@ def dist_setup():
 def run_reference(args, wl, world, rank):
     if rank != 0:
         return 0
-    import oracle as O  # noqa: F401
-    table = None
-    from oracle import optimal_composition
-    table, _ = optimal_composition(wl.l, wl.T, safety=1.01)
+    import oracle as O
+    table, _ = O.optimal_composition(wl.l, wl.T, safety=1.01)
     # each step: one matrix (cycling) through the FP64 iteration
     n = len(wl.matrices)
     for i in range(args.warmup):
@@ -238,8 +236,7 @@ def run_reference(args, wl, world, rank):
     for i in range(args.steps):
         G = wl.matrices[i % n]
         t0 = time.perf_counter()
-        import oracle
-        oracle.polar_express(G, table)
+        O.polar_express(G, table)
         tot_t += time.perf_counter() - t0
         tot_f += algorithmic_flops([G.shape], wl.T)
     val = tot_f / tot_t / 1e12

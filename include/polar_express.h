@@ -47,7 +47,7 @@ typedef enum {
     PE_ECUDA = 3,         /* a CUDA runtime/driver call failed, or a non-finite norm */
     PE_ENOCONV = 4,       /* the Remez iteration hit its iteration cap */
     PE_ETIMEOUT = 5,      /* a bounded device wait expired (results invalid) */
-    PE_EUNSUPPORTED = 6   /* valid request this build or device cannot run */
+    PE_EUNSUPPORTED = 6   /* valid request that the library or the device does not support */
 } pe_status;
 
 /* Arithmetic of the online stage. */
