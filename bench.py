@@ -301,7 +301,9 @@ def main():
                     help="error vs iteration count and vs time for FP32, BF16, BF16x3 and Newton-Schulz "
                          "(ill-conditioned workload)")
     args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
+    if args.steps < 1:
+        ap.error("--steps must be >= 1")
+    args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
 
     world, rank, local = dist_setup()
     wl = WORKLOADS[args.workload]()

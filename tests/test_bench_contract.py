@@ -1,0 +1,80 @@
+"""bench.py on the CPU: the reference arm (the FP64 oracle timed on the host
+cores) prints one JSON line with the contract's keys, N > 1 ranks other than
+rank 0 print nothing, and the flop / byte / traffic helpers agree with their
+definitions (3 s^2 L + s^3 algorithmic flops per step, Gram and A^2 counted
+once; 6 s L + 6 s^2 BF16 bytes; traffic only for the recorded kernel hash).
+"""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_flop_and_byte_counts():
+    assert bench.algorithmic_flops([(768, 3072)], 1) == 3 * 768 ** 2 * 3072 + 768 ** 3
+    assert bench.algorithmic_flops([(3072, 768)], 5) == 5 * (3 * 768 ** 2 * 3072 + 768 ** 3)
+    assert bench.dense_equiv_flops([(100, 40)], 2) == 2 * (4 * 40 ** 2 * 100 + 2 * 40 ** 3)
+    assert bench.algorithmic_bytes_bf16([(64, 256)], 1) == 6 * 64 * 256 + 6 * 64 * 64
+    # the GPT-2-small step: 217 GFLOP per polynomial step
+    import synth
+    f = bench.algorithmic_flops(synth.gpt2_small_shapes() if hasattr(synth, "gpt2_small_shapes") else
+                                [(768, 2304), (768, 768), (768, 3072), (3072, 768)] * 12, 1)
+    assert abs(f - 2.174e11) < 1e9
+
+
+def test_traffic_only_for_the_recorded_kernel_source():
+    h = bench.kernel_source_hash("umma_step")
+    assert len(h) == 16 and h == bench.kernel_source_hash("umma_step")
+    with open(os.path.join(ROOT, "profiles", "traffic.txt")) as fh:
+        rows = [ln.split() for ln in fh if ln.strip() and not ln.startswith("#")]
+    for wl, kern, hsh, nbytes in rows:
+        got = bench.committed_traffic(wl, kern)
+        assert got == (float(nbytes) if hsh == bench.kernel_source_hash(kern) else None)
+    assert bench.committed_traffic("no_such_workload", "umma_step") is None
+
+
+def _run(args, env=None):
+    e = dict(os.environ)
+    e.update(env or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, cwd=ROOT, env=e,
+                          capture_output=True, text=True, timeout=600)
+
+
+def test_reference_arm_json_line():
+    p = _run(["--impl", "reference", "--steps", "2", "--warmup", "3", "--workload", "plain_small"])
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "e2e", "cpu_baseline"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["value"] > 0
+    assert d["steps"] == 2 and d["warmup"] >= 3
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["config"]["workload"]
+
+
+def test_reference_arm_other_ranks_print_nothing():
+    p = _run(["--impl", "reference", "--steps", "1", "--warmup", "3", "--workload", "plain_small"],
+             env={"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert p.returncode == 0, p.stderr[-2000:]
+    assert p.stdout.strip() == ""
+
+
+@pytest.mark.parametrize("argv", [["--steps", "0"], ["--warmup", "1", "--steps", "2"]])
+def test_timing_rules_enforced(argv):
+    """K >= 1 timed steps and W >= 3 warm-up steps (a smaller W is raised to 3)."""
+    p = _run(["--impl", "reference", "--workload", "plain_small"] + argv)
+    if "--steps" in argv and argv[argv.index("--steps") + 1] == "0":
+        assert p.returncode == 2 and "--steps must be >= 1" in p.stderr
+    else:
+        assert p.returncode == 0, p.stderr[-2000:]
+        assert json.loads(p.stdout.strip().splitlines()[-1])["warmup"] >= 3
