@@ -22,9 +22,7 @@ def test_flop_and_byte_counts():
     assert bench.dense_equiv_flops([(100, 40)], 2) == 2 * (4 * 40 ** 2 * 100 + 2 * 40 ** 3)
     assert bench.algorithmic_bytes_bf16([(64, 256)], 1) == 6 * 64 * 256 + 6 * 64 * 64
     # the GPT-2-small step: 217 GFLOP per polynomial step
-    import synth
-    f = bench.algorithmic_flops(synth.gpt2_small_shapes() if hasattr(synth, "gpt2_small_shapes") else
-                                [(768, 2304), (768, 768), (768, 3072), (3072, 768)] * 12, 1)
+    f = bench.algorithmic_flops([(768, 2304), (768, 768), (768, 3072), (3072, 768)] * 12, 1)
     assert abs(f - 2.174e11) < 1e9
 
 
