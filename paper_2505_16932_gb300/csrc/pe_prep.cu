@@ -113,8 +113,10 @@ __device__ __forceinline__ void put4(const DevMat& M, int outputs, int64_t o, fl
     }
 }
 
+// Three blocks per SM without the momentum path (80 registers; the loads
+// of three blocks in flight), two with it (its extra loads need the registers).
 template <bool MUON>
-__global__ void __launch_bounds__(256) prepare_kernel(const DevMat* __restrict__ mats, int nmats,
+__global__ void __launch_bounds__(256, MUON ? 2 : 3) prepare_kernel(const DevMat* __restrict__ mats, int nmats,
                                                       const TileTask* __restrict__ tiles,
                                                       double* __restrict__ partials, float scale, float eps,
                                                       int outputs, float* __restrict__ nscale,
