@@ -70,12 +70,14 @@ def _worker(rank, world, port, mode, out):
             pass
 
 
-@pytest.mark.parametrize("mode", ["ok", "dead"])
-def test_sharded_gloo_two_ranks(mode):
+@pytest.mark.parametrize("world,mode", [(2, "ok"), (2, "dead"), (3, "ok")])
+def test_sharded_gloo_ranks(world, mode):
+    """Whole matrices over 2 or 3 gloo ranks (with 5 matrices, 3 ranks own
+    uneven counts and byte totals, so the all-gather pads to the largest)."""
     ctx = mp.get_context("spawn")
-    out = ctx.Array("i", [-1, -1])
+    out = ctx.Array("i", [-1] * world)
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, mode, out)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, mode, out)) for r in range(world)]
     for p in procs:
         p.start()
     for p in procs:
@@ -84,7 +86,7 @@ def test_sharded_gloo_two_ranks(mode):
             p.kill()
             pytest.fail("rank did not finish")
     if mode == "ok":
-        assert list(out) == [1, 1]
+        assert list(out) == [1] * world
     else:
         assert out[0] == 2          # the survivor's collective failed, it did not hang
 
