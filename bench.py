@@ -285,6 +285,44 @@ def committed_traffic(workload: str, kernel: str):
     return None
 
 
+def roofline_line(trace, shapes, dtype, flops_step, in_bytes, workload, peaks):
+    """Roofline of the dominant kernel (largest traced time): algorithmic
+    flops (or bytes) per launch over its mean CUDA-event launch time, against
+    the measured burst peak (and the sustained one for tensor-bound kernels);
+    DRAM traffic from the committed ncu figure while the source matches."""
+    dom_name, (dom_n, dom_ms) = max(trace.items(), key=lambda kv: kv[1][1])
+    dom_avg_ms = dom_ms / dom_n
+    tot_trace_ms = sum(v[1] for v in trace.values())
+    if dom_name in ("umma_step", "simt_update", "umma_update", "umma_gram", "umma_square", "simt_gram",
+                    "simt_square"):
+        if dom_name == "umma_step":
+            f_launch = flops_step
+        else:
+            f_launch = 0.0
+            key = dom_name.split("_")[1]
+            for m, n in shapes:
+                s, L = min(m, n), max(m, n)
+                f_launch += {"gram": s * s * L, "square": float(s) ** 3, "update": 2.0 * s * s * L}[key]
+        achieved = f_launch / (dom_avg_ms * 1e-3) / 1e12
+        if dtype == "fp32":
+            # FP32 SIMT roof: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock
+            peak, unit, bound = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12, "TFLOP/s", "alu"
+        else:
+            peak, unit, bound = peaks["bf16_tflops"], "TFLOP/s", "tensor"
+    else:
+        achieved = in_bytes * 2 / (dom_avg_ms * 1e-3) / 1e9
+        peak, unit, bound = peaks["hbm_gbs"], "GB/s", "hbm"
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": committed_traffic(workload, dom_name), "kernel": dom_name, "kernel_ms_avg": dom_avg_ms,
+                "launches_traced": dom_n, "share_of_step": dom_ms / tot_trace_ms,
+                "peak_source": peaks["source"] + " burst",
+                "algorithmic_bytes_per_launch_bf16": algorithmic_bytes_bf16(shapes, 1)}
+    if bound == "tensor":
+        roofline["peak_sustained"] = peaks["bf16_tflops_sustained"]
+        roofline["frac_sustained"] = achieved / peaks["bf16_tflops_sustained"]
+    return roofline
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -414,39 +452,7 @@ def main():
     pe.pe_sync_status()
 
     # ---------------------------------------------------------- roofline
-    peaks = measured_peaks()
-    dom = max(trace.items(), key=lambda kv: kv[1][1])
-    dom_name, (dom_n, dom_ms) = dom
-    dom_avg_ms = dom_ms / dom_n
-    tot_trace_ms = sum(v[1] for v in trace.values())
-    if dom_name in ("umma_step", "simt_update", "umma_update", "umma_gram", "umma_square", "simt_gram",
-                    "simt_square"):
-        if dom_name == "umma_step":
-            f_launch = flops_step
-        else:
-            f_launch = 0.0
-            for m, n in shapes:
-                s, L = min(m, n), max(m, n)
-                key = dom_name.split("_")[1]
-                f_launch += {"gram": s * s * L, "square": float(s) ** 3, "update": 2.0 * s * s * L}[key]
-        achieved = f_launch / (dom_avg_ms * 1e-3) / 1e12
-        if dtype == "fp32":
-            # FP32 SIMT roof: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock
-            peak, unit, bound = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12, "TFLOP/s", "alu"
-        else:
-            peak, unit, bound = peaks["bf16_tflops"], "TFLOP/s", "tensor"
-    else:
-        f_launch = None
-        achieved = in_bytes * 2 / (dom_avg_ms * 1e-3) / 1e9
-        peak, unit, bound = peaks["hbm_gbs"], "GB/s", "hbm"
-    traffic = committed_traffic(wl.name, dom_name)
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": traffic, "kernel": dom_name, "kernel_ms_avg": dom_avg_ms, "launches_traced": dom_n,
-                "share_of_step": dom_ms / tot_trace_ms, "peak_source": peaks["source"] + " burst",
-                "algorithmic_bytes_per_launch_bf16": algorithmic_bytes_bf16(shapes, 1)}
-    if bound == "tensor":
-        roofline["peak_sustained"] = peaks["bf16_tflops_sustained"]
-        roofline["frac_sustained"] = achieved / peaks["bf16_tflops_sustained"]
+    roofline = roofline_line(trace, shapes, dtype, flops_step, in_bytes, wl.name, measured_peaks())
 
     # ------------------------------------------ extras (rank 0, N = 1 style)
     extras = {}

@@ -76,3 +76,27 @@ def test_timing_rules_enforced(argv):
     else:
         assert p.returncode == 0, p.stderr[-2000:]
         assert json.loads(p.stdout.strip().splitlines()[-1])["warmup"] >= 3
+
+
+def test_roofline_line():
+    """The dominant kernel's roofline from a traced launch list: the fused
+    step kernel against the BF16 peaks (burst and sustained), a phase kernel
+    with its own flops, the FP32 path against the derived SIMT roof, and a
+    memory-bound kernel against HBM."""
+    peaks = {"hbm_gbs": 6000.0, "bf16_tflops": 2000.0, "bf16_tflops_sustained": 1600.0, "sm_max_mhz": 2000.0,
+             "source": "measured"}
+    shapes = [(768, 3072), (3072, 768)]
+    fs = bench.algorithmic_flops(shapes, 1)
+    r = bench.roofline_line({"prepare": (5, 0.5), "umma_step": (25, 25 * 0.25)}, shapes, "bf16", fs, 1e8,
+                            "no_such_workload", peaks)
+    assert r["kernel"] == "umma_step" and r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - fs / 0.25e-3 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 2000.0) < 1e-12 and abs(r["frac_sustained"] - r["achieved"] / 1600.0) < 1e-12
+    assert r["traffic"] is None and abs(r["share_of_step"] - 6.25 / 6.75) < 1e-12
+    r = bench.roofline_line({"umma_update": (10, 1.0), "umma_gram": (10, 0.5)}, shapes, "bf16", fs, 1e8, "x", peaks)
+    assert r["kernel"] == "umma_update"
+    assert abs(r["achieved"] - 2 * 2.0 * 768 ** 2 * 3072 / 0.1e-3 / 1e12) < 1e-6
+    r = bench.roofline_line({"simt_update": (10, 1.0)}, shapes, "fp32", fs, 1e8, "x", peaks)
+    assert r["bound"] == "alu" and abs(r["peak"] - 152 * 128 * 2 * 2000e6 / 1e12) < 1e-9 and "frac_sustained" not in r
+    r = bench.roofline_line({"prepare": (4, 2.0)}, shapes, "bf16", fs, 1e8, "x", peaks)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and abs(r["achieved"] - 2e8 / 0.5e-3 / 1e9) < 1e-9
