@@ -300,6 +300,39 @@ def test_injected_alloc_failure():
     assert ei.value.code == pe.PE_ENOMEM
 
 
+SENTINEL = 12345.0
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "bf16", "bf16x3"])
+@pytest.mark.parametrize("m,n", [(130, 257), (257, 130), (1, 77), (256, 512)])
+def test_writes_stay_inside_the_matrix(dtype, m, n):
+    """Canaries: a call writes exactly the caller's m x n elements. Guard
+    elements before the first and after the last element of the same
+    allocation keep their sentinel, and so do the padding columns between rows
+    when the leading dimension exceeds n (odd and 16-byte-multiple pitches:
+    element stores and TMA stores); the strided result equals the contiguous
+    one bit for bit."""
+    rng = np.random.default_rng(7 * m + n)
+    G = torch.from_numpy(rng.standard_normal((m, n)).astype(np.float32)).cuda()
+    tab = table(1e-3, 3)
+    guard = 1024   # floats: keeps the matrix 16-byte aligned
+    buf = torch.full((guard + m * n + guard,), SENTINEL, device="cuda")
+    X = buf[guard:guard + m * n].view(m, n)
+    X.copy_(G)
+    pe.pe_polar(X, tab, dtype)
+    pe.pe_sync_status()
+    assert torch.all(buf[:guard] == SENTINEL) and torch.all(buf[guard + m * n:] == SENTINEL)
+    for ld in (n + 5, (n + 3) // 4 * 4 + 8):
+        buf2 = torch.full((guard + m * ld + guard,), SENTINEL, device="cuda")
+        Y = buf2[guard:guard + m * ld].view(m, ld)
+        Y[:, :n].copy_(G)
+        pe.pe_polar(Y[:, :n], tab, dtype)
+        pe.pe_sync_status()
+        assert torch.all(buf2[:guard] == SENTINEL) and torch.all(buf2[guard + m * ld:] == SENTINEL), ld
+        assert torch.all(Y[:, n:] == SENTINEL), ld
+        assert torch.equal(Y[:, :n], X), ld
+
+
 def test_empty_and_bad_shapes_rejected():
     X = torch.zeros((0, 5), device="cuda")
     with pytest.raises(pe.PolarExpressError):
