@@ -273,10 +273,12 @@ int pe_debug_set(int key, int64_t value);
  * The paper has no counterpart; this is a deployment variant of the same
  * computation.
  *
- * Who needs it: code recorded into a CUDA graph in global capture mode (where
- * cudaMalloc is not allowed), programs whose own allocator owns device memory
- * up front (a framework's caching pool, a server with a fixed memory budget),
- * and loops that cannot afford the implicit synchronisation of an allocation.
+ * Who needs it: programs whose own allocator takes all of device memory up
+ * front (a framework's caching pool, an inference server with a fixed memory
+ * budget), where an allocation by a library fails or fragments memory the
+ * program has already accounted for; loops that cannot afford the
+ * device-wide synchronisation that cudaMalloc and cudaFree can imply; hosts
+ * that load this library as a plug-in that must allocate nothing.
  *
  * Workspace: a file-scope device array of 32 MiB inside the library, present
  * on every GPU where the library is loaded from load until process exit. The
@@ -284,19 +286,20 @@ int pe_debug_set(int key, int64_t value);
  * s' = min(m,n) and L' = max(m,n) rounded up to multiples of 128: e.g. every
  * GPT-2-small Muon matrix (768 x 3072 and smaller), or 1024 x 2048. Larger
  * matrices are rejected with PE_EINVAL and a message naming both sizes.
- * It calls no cudaMalloc, cudaFree or other allocating routine.
+ * It calls no cudaMalloc, cudaFree or other allocating routine, and copies
+ * nothing from host memory: a set-up kernel writes the descriptors.
  *
  * Sharing: all calls on a device use the same array, which keeps the last
- * call's contents; each call reloads its descriptors and clears what must
- * start at zero. Calls whose work overlaps on the GPU (different streams
- * without ordering between them) race on the array and give wrong results:
- * issue them on one stream or order the streams. The descriptors are staged
- * with cudaMemcpyAsync from host memory, which orders the copy after work
- * already queued on `stream`.
+ * call's contents; each call rewrites its descriptors and task lists and
+ * clears what must start at zero. Calls whose work overlaps on the GPU
+ * (different streams without ordering between them) race on the array and
+ * give wrong results: issue them on one stream or order the streams.
  *
  * First call on a device: looks up the array's device address with
- * cudaGetSymbolAddress (which may load the module); make that first call
- * before any stream capture that should contain later calls.
+ * cudaGetSymbolAddress (which may load the module) and keeps it for the
+ * process; make that first call before any stream capture. After
+ * cudaDeviceReset the kept address is stale: this entry point does not
+ * support a device reset.
  *
  *   X, m, n, table, T, stream  as for pe_polar (X: m x n row-major FP32, ld = n,
  *                              in/out, device memory).

@@ -2,18 +2,23 @@
 // of its device workspace in one fixed, file-scope device array instead of
 // memory obtained from cudaMalloc.
 //
-// Some callers cannot let a library allocate device memory: code that is
-// being captured into a CUDA graph in global capture mode (cudaMalloc is an
-// illegal call there), applications whose allocator owns all of device
-// memory up front (a framework's caching pool, an inference server with a
-// fixed memory budget), and latency-critical loops that must never hit the
-// allocator's implicit synchronisation. For them this entry point uses a
-// static workspace of kScratchBytes that exists, on every GPU where the
-// library is loaded, from module load until process exit.
+// Some callers cannot let a library allocate device memory: applications
+// whose own allocator takes all of device memory up front (a framework's
+// caching pool, an inference server with a fixed memory budget), where a
+// library's cudaMalloc either fails or fragments memory the application
+// already accounted for; latency-critical loops that must never block on
+// the device-wide synchronisation that cudaMalloc and cudaFree can imply;
+// and hosts that load this library as a plug-in under a rule that plug-ins
+// allocate nothing. For them this entry point uses a static workspace of
+// kScratchBytes that exists, on every GPU where the library is loaded, from
+// module load until process exit.
 //
-// The array's name is only a host-side stand-in in host code; its device
-// address is looked up once per device with cudaGetSymbolAddress (first call
-// on that device) and passed to the kernels.
+// In host code the array's name is only a stand-in, not a device address:
+// its device address is looked up once per device with cudaGetSymbolAddress
+// (the first call on that device) and passed to the kernels. Nothing is
+// staged from host memory: a set-up kernel takes the matrix descriptor by
+// value and writes it, the task lists and the cleared prepare ticket into
+// the array, then the prepare and SIMT kernels of the FP32 path run on it.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -34,13 +39,36 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_na_mu;
 void* g_na_ptr[kMaxDevices] = {nullptr};
-TileTask g_na_tiles[kMaxTiles];   // host staging of the task lists (under g_na_mu)
 
 inline int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 int na_fail(int code, const std::string& m) {
     set_last_error(m.c_str());
     return code;
+}
+
+// Writes the descriptor M to *d_mat, the task lists to `t` (prepare strips,
+// then the Gram and square tiles on and above the diagonal, then the update
+// tiles, in the order of the host loops of pe_polar's FP32 plan) and clears
+// the 64-byte ticket / status block. One block; thread k takes rows k,
+// k + blockDim, ... of each list.
+__global__ void na_setup_kernel(DevMat M, DevMat* d_mat, TileTask* t, int nb, int ts, int tl, unsigned* ticket) {
+    if (threadIdx.x == 0) *d_mat = M;
+    if (threadIdx.x < 16) ticket[threadIdx.x] = 0u;
+    const int rows_p = M.sp / kPrepRows;
+    const int n_prep = rows_p * nb;
+    const int n_sym = ts * (ts + 1) / 2;
+    for (int a = threadIdx.x; a < rows_p; a += blockDim.x)
+        for (int b = 0; b < nb; ++b) t[a * nb + b] = TileTask{0, a, b, -1};
+    for (int a = threadIdx.x; a < ts; a += blockDim.x) {
+        const int row0 = a * ts - a * (a - 1) / 2;   // tiles (a', b), a' < a, b >= a'
+        for (int b = a; b < ts; ++b) {
+            t[n_prep + row0 + (b - a)] = TileTask{0, a, b, kGram};
+            t[n_prep + n_sym + row0 + (b - a)] = TileTask{0, a, b, kSquare};
+        }
+    }
+    for (int a = threadIdx.x; a < ts; a += blockDim.x)
+        for (int b = 0; b < tl; ++b) t[n_prep + 2 * n_sym + a * tl + b] = TileTask{0, a, b, kApply};
 }
 
 }  // namespace
@@ -59,7 +87,8 @@ extern "C" int pe_polar_noalloc(void* X, int64_t m, int64_t n, const double* tab
     const int64_t s = std::min(m, n), L = std::max(m, n);
     const int64_t sp = rup(s, kPadS), Lp = rup(L, kPadL);
     // workspace layout: [descriptor | tasks | partials | scale | ticket | X | X' | A | B]
-    const int64_t n_prep = (sp / kPrepRows) * ((Lp + kPrepCols - 1) / kPrepCols);
+    const int64_t nb = (Lp + kPrepCols - 1) / kPrepCols;
+    const int64_t n_prep = (sp / kPrepRows) * nb;
     const int64_t ts = sp / 128, tl = Lp / 128;
     const int64_t n_sym = ts * (ts + 1) / 2, n_app = ts * tl;
     const int64_t n_tasks = n_prep + 2 * n_sym + n_app;
@@ -84,6 +113,8 @@ extern "C" int pe_polar_noalloc(void* X, int64_t m, int64_t n, const double* tab
     if (e != cudaSuccess) return na_fail(PE_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return na_fail(PE_EUNSUPPORTED, "device index out of range");
     if (!g_na_ptr[dev]) {
+        // set-up, once per device (this device is current): the array's
+        // device address
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
@@ -111,44 +142,31 @@ extern "C" int pe_polar_noalloc(void* X, int64_t m, int64_t n, const double* tab
     M.xf2 = reinterpret_cast<float*>(base + o_xf2);
     M.af = reinterpret_cast<float*>(base + o_af);
     M.bfp = reinterpret_cast<float*>(base + o_bf);
-    TileTask* t = g_na_tiles;
-    int k = 0;
-    for (int a = 0; a < sp / kPrepRows; ++a)
-        for (int b = 0; b < (Lp + kPrepCols - 1) / kPrepCols; ++b) t[k++] = TileTask{0, a, b, -1};
-    const int g0 = k;
-    for (int a = 0; a < ts; ++a)
-        for (int b = a; b < ts; ++b) t[k++] = TileTask{0, a, b, kGram};
-    const int s0 = k;
-    for (int a = 0; a < ts; ++a)
-        for (int b = a; b < ts; ++b) t[k++] = TileTask{0, a, b, kSquare};
-    const int a0 = k;
-    for (int a = 0; a < ts; ++a)
-        for (int b = 0; b < tl; ++b) t[k++] = TileTask{0, a, b, kApply};
 
-    const DevMat* d_mat = reinterpret_cast<const DevMat*>(base + o_mat);
+    DevMat* d_mat = reinterpret_cast<DevMat*>(base + o_mat);
     TileTask* d_tasks = reinterpret_cast<TileTask*>(base + o_tasks);
     double* d_part = reinterpret_cast<double*>(base + o_part);
     float* d_scale = reinterpret_cast<float*>(base + o_scale);
     unsigned* d_ticket = reinterpret_cast<unsigned*>(base + o_ticket);
     int* d_status = reinterpret_cast<int*>(base + o_ticket + 16);
-    // the previous call's contents stay in the array: reload the descriptors
-    // and clear the prepare ticket and the status word
-    e = cudaMemcpyAsync(base + o_mat, &M, sizeof(M), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tasks, t, sizeof(TileTask) * k, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_ticket, 0, 64, st);
-    if (e != cudaSuccess) return na_fail(PE_ECUDA, std::string("staging descriptors: ") + cudaGetErrorString(e));
-    e = launch_prepare(d_mat, 1, d_tasks, n_prep, d_part, 1.01f, 1e-7f, kPrepF32, d_scale, d_status, d_status + 1, 0,
-                       d_ticket, st);
+    const int g0 = (int)n_prep, q0 = (int)(n_prep + n_sym), a0 = (int)(n_prep + 2 * n_sym);
+    // the previous call's contents stay in the array: the set-up kernel
+    // rewrites the descriptor and task lists and clears the ticket and status
+    na_setup_kernel<<<1, 256, 0, st>>>(M, d_mat, d_tasks, (int)nb, (int)ts, (int)tl, d_ticket);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = launch_prepare(d_mat, 1, d_tasks, (int)n_prep, d_part, 1.01f, 1e-7f, kPrepF32, d_scale, d_status,
+                           d_status + 1, 0, d_ticket, st);
     for (int step = 0; step < T && e == cudaSuccess; ++step) {
         const float a = (float)table[3 * step], b = (float)table[3 * step + 1], c = (float)table[3 * step + 2];
         const int last = (step == T - 1);
-        e = launch_simt_phase(d_mat, d_tasks + g0, s0 - g0, kGram, a, b, c, step & 1, last, step == 0, d_scale, st);
+        e = launch_simt_phase(d_mat, d_tasks + g0, q0 - g0, kGram, a, b, c, step & 1, last, step == 0, d_scale, st);
         if (e == cudaSuccess)
-            e = launch_simt_phase(d_mat, d_tasks + s0, a0 - s0, kSquare, a, b, c, step & 1, last, step == 0, d_scale,
+            e = launch_simt_phase(d_mat, d_tasks + q0, a0 - q0, kSquare, a, b, c, step & 1, last, step == 0, d_scale,
                                   st);
         if (e == cudaSuccess)
-            e = launch_simt_phase(d_mat, d_tasks + a0, k - a0, kApply, a, b, c, step & 1, last, step == 0, d_scale,
-                                  st);
+            e = launch_simt_phase(d_mat, d_tasks + a0, (int)n_tasks - a0, kApply, a, b, c, step & 1, last,
+                                  step == 0, d_scale, st);
     }
     if (e != cudaSuccess) return na_fail(PE_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
     return PE_OK;
