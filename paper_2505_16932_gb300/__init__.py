@@ -326,7 +326,7 @@ def pe_launch_count() -> int:
 
 
 TRACE_KINDS = ["norm_partials", "prepare", "simt_gram", "simt_square", "simt_update", "umma_step",
-               "umma_gram", "umma_square", "umma_update"]
+               "umma_gram", "umma_square", "umma_update", "simt_gram_reduce"]
 
 
 def pe_trace_enable(on: bool = True):

@@ -35,7 +35,7 @@ bool g_dbg_fail_alloc = false;
 void* g_dbg_prof = nullptr;
 int g_dbg_bk = 0;      // 0: default k-block
 int g_dbg_order = -1;  // -1: default tile order
-int g_dbg_mode = -1;   // -1: autotuned; 0 / 1 / 2: force the tcgen05 kernel mode
+int g_dbg_mode = -1;   // -1: autotuned; 0 / 2: force the tcgen05 kernel mode
 int g_dbg_nacc = 0;    // 0: default accumulators of 2-SM plans; 1 or 2
 bool g_dbg_nopair = false;   // true: no packing of small matrices in plans built from now on
 
@@ -121,6 +121,10 @@ int device_state(DeviceState** out) {
 
 // ------------------------------------------------------------------ plans
 
+// FP32 path: Gram reductions longer than this run in chunks (see pe_simt.cu)
+constexpr int64_t kGramChunk = 4096;
+constexpr int kMaxGramChunks = 256;
+
 // internal plan flags (above the public PE_BATCH_* bits)
 constexpr unsigned kFlagSplit = 1u << 16;           // long-side split plan (pe_split_*)
 constexpr unsigned kFlagSplitShortCols = 1u << 17;  // split plan whose shared short side is the columns
@@ -156,6 +160,8 @@ struct Plan {
     int n_prep = 0;
     TileTask* d_tiles[3] = {nullptr, nullptr, nullptr};   // SIMT per-phase lists
     int n_tiles[3] = {0, 0, 0};
+    TileTask* d_red = nullptr;    // SIMT: tiles of split Grams (partials summed by the reduce launch)
+    int n_red = 0;
     int* d_counters = nullptr;
     int n_counters = 0;
     UmmaPlan umma;                // tcgen05 path (tensor maps, persistent schedule)
@@ -236,8 +242,8 @@ int build_plan(const PlanKey& key, Plan** out) {
     Carve cv;
     // layout of the single workspace allocation
     const size_t o_mats = cv.take(sizeof(DevMat) * count, 64);
-    std::vector<TileTask> prep, tl[3];
-    struct Off { size_t xf, xf2, xh0, xh1, xl0, xl1, xq, af, ah, al, bfp, bh, bl; };
+    std::vector<TileTask> prep, tl[3], red;
+    struct Off { size_t xf, xf2, xh0, xh1, xl0, xl1, xq, af, ah, al, bfp, bh, bl, gpart, btr; };
     std::vector<Off> offs(count);
     int part = 0;
     for (int i = 0; i < count; ++i) {
@@ -290,12 +296,25 @@ int build_plan(const PlanKey& key, Plan** out) {
             o.xf2 = cv.take(4 * sL);
             o.af = cv.take(4 * ss);
             o.bfp = cv.take(4 * ss);
+            // Gram reductions longer than kGramChunk run as chunks of at most
+            // kGramChunk columns (at most kMaxGramChunks of them, and at most
+            // 1 GiB of partial Grams per matrix)
+            int ks = 1;
+            if (!(key.flags & kFlagSplit) && M.Lp > kGramChunk) {
+                ks = (int)std::min<int64_t>((M.Lp + kGramChunk - 1) / kGramChunk, kMaxGramChunks);
+                while (ks > 1 && (size_t)ks * 4 * ss > ((size_t)1 << 30)) --ks;
+            }
+            const int64_t chunk = round_up((M.Lp + ks - 1) / ks, 16);
+            M.ksplit = (int32_t)((M.Lp + chunk - 1) / chunk);
+            M.kchunk = (int32_t)chunk;
+            if (M.ksplit > 1) o.gpart = cv.take(4 * ss * (size_t)M.ksplit);
         } else {
             o.xh0 = cv.take(2 * sL);
             o.xh1 = cv.take(2 * sL);
             o.ah = cv.take(2 * ss);
             o.bh = cv.take(2 * ss);
             if (dtype == PE_BF16) o.xq = cv.take(sL);
+            if (dtype == PE_BF16) o.btr = cv.take(4 * (size_t)(2 * (M.sp / 32)), 64);   // tr(B), tr(A) parts
             if (dtype == PE_BF16 && (key.flags & kFlagSplit)) o.af = cv.take(4 * ss);   // partial Gram, FP32
             if (dtype == PE_BF16X3) {
                 o.xf = cv.take(4 * sL);
@@ -310,7 +329,12 @@ int build_plan(const PlanKey& key, Plan** out) {
             const int ts = M.sp / 128, tL = M.Lp / 128;
             for (int a = 0; a < ts; ++a)
                 for (int b = a; b < ts; ++b) {
-                    tl[kGram].push_back(TileTask{i, a, b, kGram});
+                    if (M.ksplit > 1) {
+                        for (int k = 0; k < M.ksplit; ++k) tl[kGram].push_back(TileTask{i, a, b, kGram | (k << 8)});
+                        red.push_back(TileTask{i, a, b, kGram});
+                    } else {
+                        tl[kGram].push_back(TileTask{i, a, b, kGram});
+                    }
                     tl[kSquare].push_back(TileTask{i, a, b, kSquare});
                 }
             for (int a = 0; a < ts; ++a)
@@ -327,6 +351,8 @@ int build_plan(const PlanKey& key, Plan** out) {
         P->n_tiles[k] = (int)tl[k].size();
         o_tl[k] = cv.take(sizeof(TileTask) * std::max<size_t>(1, tl[k].size()), 64);
     }
+    P->n_red = (int)red.size();
+    const size_t o_red = cv.take(sizeof(TileTask) * std::max<size_t>(1, red.size()), 64);
     P->n_counters = 2 * count + 64;
     const size_t o_cnt = cv.take(sizeof(int) * P->n_counters, 64);
     size_t o_umma = 0, umma_bytes = 0;
@@ -356,12 +382,14 @@ int build_plan(const PlanKey& key, Plan** out) {
             M.xf2 = reinterpret_cast<float*>(base + o.xf2);
             M.af = reinterpret_cast<float*>(base + o.af);
             M.bfp = reinterpret_cast<float*>(base + o.bfp);
+            if (M.ksplit > 1) M.gpart = reinterpret_cast<float*>(base + o.gpart);
         } else {
             M.xh[0] = reinterpret_cast<bf16*>(base + o.xh0);
             M.xh[1] = reinterpret_cast<bf16*>(base + o.xh1);
             M.ah = reinterpret_cast<bf16*>(base + o.ah);
             M.bh = reinterpret_cast<bf16*>(base + o.bh);
             if (dtype == PE_BF16) M.xq = reinterpret_cast<int8_t*>(base + o.xq);
+            if (dtype == PE_BF16) M.btr = reinterpret_cast<float*>(base + o.btr);
             if (dtype == PE_BF16 && (key.flags & kFlagSplit)) M.af = reinterpret_cast<float*>(base + o.af);
             if (dtype == PE_BF16X3) {
                 M.xf = reinterpret_cast<float*>(base + o.xf);
@@ -379,6 +407,7 @@ int build_plan(const PlanKey& key, Plan** out) {
     P->d_ticket = reinterpret_cast<unsigned*>(base + o_ticket);
     P->d_prep = reinterpret_cast<TileTask*>(base + o_prep);
     for (int k = 0; k < 3; ++k) P->d_tiles[k] = reinterpret_cast<TileTask*>(base + o_tl[k]);
+    P->d_red = reinterpret_cast<TileTask*>(base + o_red);
     P->d_counters = reinterpret_cast<int*>(base + o_cnt);
     // zero the whole workspace once: the padding of every canonical buffer
     // stays zero from here on (prepare skips strips of padding rows), and the
@@ -393,6 +422,8 @@ int build_plan(const PlanKey& key, Plan** out) {
         if (!tl[k].empty())
             PE_CU(cudaMemcpy(P->d_tiles[k], tl[k].data(), sizeof(TileTask) * tl[k].size(),
                              cudaMemcpyHostToDevice));
+    if (!red.empty())
+        PE_CU(cudaMemcpy(P->d_red, red.data(), sizeof(TileTask) * red.size(), cudaMemcpyHostToDevice));
     PE_CU(cudaMemset(P->d_counters, 0, sizeof(int) * P->n_counters));
     if (dtype != PE_FP32) {
         const bool tune = false;   // schedules are tuned after the plan is cached (autotune)
@@ -441,10 +472,17 @@ int enqueue(Plan* P, cudaStream_t st, bool tuning = false) {
         const int last = (!tuning && t == k.T - 1);
         if (k.dtype == PE_FP32) {
             for (int ph = 0; ph < 3; ++ph) {
-                TraceScope ts(2 + ph, st);
-                PE_CU(launch_simt_phase(P->d_mats, P->d_tiles[ph], P->n_tiles[ph], ph, a, b, c, t & 1,
-                                        last, t == 0, P->d_nscale, st));
-                ++nk;
+                {
+                    TraceScope ts(2 + ph, st);
+                    PE_CU(launch_simt_phase(P->d_mats, P->d_tiles[ph], P->n_tiles[ph], ph, a, b, c, t & 1,
+                                            last, t == 0, P->d_nscale, st));
+                    ++nk;
+                }
+                if (ph == kGram && P->n_red) {
+                    TraceScope ts(9, st);
+                    PE_CU(launch_simt_gram_reduce(P->d_mats, P->d_red, P->n_red, t == 0, P->d_nscale, st));
+                    ++nk;
+                }
             }
         } else {
             const bool phased = (k.flags & PE_BATCH_PHASED) != 0;
@@ -537,7 +575,7 @@ int autotune(Plan* P, cudaStream_t st) {
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
         const int mode = it->second / 16, order = it->second % 16;
-        if ((mode == 1 && P->umma.max_clusters < 1) || (mode == 2 && P->umma.max_clusters2 < 1))
+        if ((mode != 0 && mode != 2) || (mode == 2 && P->umma.max_clusters2 < 1))
             return PE_OK;   // cached on another configuration
         P->umma.mode = mode;
         return umma_schedule(&P->umma, order, &g_err);
@@ -553,7 +591,6 @@ int autotune(Plan* P, cudaStream_t st) {
     if (g_dbg_mode >= 0) modes.push_back(P->umma.mode);
     else {
         modes.push_back(0);
-        if (P->umma.max_clusters > 0) modes.push_back(1);
         if (P->umma.max_clusters2 > 0) modes.push_back(2);
     }
     // Round robin over the candidates (a warm-up pass, then two timed passes,
@@ -1166,7 +1203,10 @@ int pe_debug_set(int key, int64_t value) {
         case 4: pe::g_dbg_prof = reinterpret_cast<void*>(value); return PE_OK;
         case 5: pe::g_dbg_bk = (int)value; return PE_OK;
         case 6: pe::g_dbg_order = (int)value; return PE_OK;
-        case 7: pe::g_dbg_mode = (int)value; return PE_OK;
+        case 7:
+            if (value != -1 && value != 0 && value != 2) return pe::fail(PE_EINVAL, "kernel mode must be -1, 0 or 2");
+            pe::g_dbg_mode = (int)value;
+            return PE_OK;
         case 8: pe::g_dbg_nacc = (int)value; return PE_OK;
         case 9: pe::g_dbg_nopair = value != 0; return PE_OK;
         default: return pe::fail(PE_EINVAL, "unknown debug key");

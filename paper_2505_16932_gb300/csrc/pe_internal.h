@@ -63,6 +63,14 @@ struct DevMat {
     bf16* xl[2];         // BF16 X lo part (BF16x3), ping-pong
     int8_t* xq;          // BF16 path: byte of the next 8 mantissa bits of X
                          // below xh[cur] (see x_split), updated in place
+    float* btr;          // BF16 path: tr(B) of the step in sp / 32 parts, one per 32-row
+                         // diagonal chunk (written by the square epilogue, or the Gram's
+                         // when c = 0 throughout), then tr(A) in sp / 32 parts (written by
+                         // the Gram epilogue); read by the update epilogue
+    int32_t ksplit;      // FP32 path: the Gram's reduction (length Lp) runs as ksplit chunks of
+    int32_t kchunk;      // kchunk columns into the partial Grams gpart, summed in chunk order
+                         // by the reduce kernel (ksplit <= 1: one pass straight into af)
+    float* gpart;        // ksplit partial Grams, each sp x sp (tiles on and above the diagonal)
     float* af;           // FP32 A = X X^T (FP32, BF16x3)
     bf16* ah;            // BF16 A (hi)
     bf16* al;            // BF16 A lo (BF16x3)
@@ -147,6 +155,10 @@ cudaError_t launch_split_load_a(const float* A, int64_t lda, int s, int sp, bf16
 cudaError_t launch_simt_phase(const DevMat* mats, const TileTask* tiles, int ntiles, int kind,
                               float a, float b, float c, int src, int last, int first,
                               const float* nscale, cudaStream_t st);
+// FP32 path, matrices with ksplit > 1: A = s^2 (sum of the partial Grams in
+// chunk order) on the tiles `tiles` (mat, tm, tn), mirrored below the diagonal
+cudaError_t launch_simt_gram_reduce(const DevMat* mats, const TileTask* tiles, int ntiles, int first,
+                                    const float* nscale, cudaStream_t st);
 
 }  // namespace pe
 #endif

@@ -5,7 +5,13 @@
 //   update  X' = a X + B X                (ping-pong X buffers; the last step
 //                                          writes the caller's layout)
 // One grouped launch per product covers every matrix of the call: block
-// i runs tile tiles[i] = (matrix, tile row, tile column).
+// i runs tile tiles[i] = (matrix, tile row, tile column). A Gram whose
+// reduction is long (L > 4096) is cut into chunks along L (TileTask::kind
+// carries the chunk index above its low byte): each block writes the
+// chunk's partial product, and a reduce launch sums the partials in chunk
+// order, so every output sums at most kchunk products in one accumulator
+// (FP32 rounding error ~ sqrt(kchunk) u instead of ~ sqrt(L) u) and a
+// tall-skinny Gram spreads over many blocks.
 //
 // 128 x 128 output tile per block, BK = 16, 256 threads, 8 x 8 outputs per
 // thread as two 4 x 4 quadrants (rows ty*4 and 64 + ty*4, same for columns),
@@ -87,6 +93,10 @@ __global__ void __launch_bounds__(256) simt_phase_kernel(const DevMat* __restric
     if (kKind == kGram) { op.a = xs; op.lda = M.Lp; op.b = xs; op.ldb = M.Lp; op.K = M.Lp; }
     else if (kKind == kSquare) { op.a = M.af; op.lda = M.sp; op.b = M.af; op.ldb = M.sp; op.K = M.sp; }
     else { op.a = M.bfp; op.lda = M.sp; op.b = xs; op.ldb = M.Lp; op.K = M.sp; }
+    // split Gram: this block's chunk [kbeg, kend) of the reduction
+    const bool part = (kKind == kGram) && M.ksplit > 1;
+    const int kbeg = part ? (tk.kind >> 8) * M.kchunk : 0;
+    const int kend = part ? min(op.K, kbeg + M.kchunk) : op.K;
 
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -97,13 +107,13 @@ __global__ void __launch_bounds__(256) simt_phase_kernel(const DevMat* __restric
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
     float4 ra[2], rb[2];
-    load_tiles<kBK>(op, r0, c0, 0, tid, ra, rb);
+    load_tiles<kBK>(op, r0, c0, kbeg, tid, ra, rb);
     store_tiles<kBK>(As[0], Bs[0], tid, ra, rb);
     __syncthreads();
-    const int nk = op.K / BK;
+    const int nk = (kend - kbeg) / BK;
     for (int kt = 0; kt < nk; ++kt) {
         const int cur = kt & 1;
-        if (kt + 1 < nk) load_tiles<kBK>(op, r0, c0, (kt + 1) * BK, tid, ra, rb);
+        if (kt + 1 < nk) load_tiles<kBK>(op, r0, c0, kbeg + (kt + 1) * BK, tid, ra, rb);
 #pragma unroll
         for (int k = 0; k < BK; ++k) {
             float av[8], bv[8];
@@ -138,7 +148,11 @@ __global__ void __launch_bounds__(256) simt_phase_kernel(const DevMat* __restric
             float v[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) v[j] = acc[i][jh * 4 + j];
-            if (kKind == kGram) {
+            if (kKind == kGram && part) {
+                // the chunk's partial product, unscaled (the reduce applies s^2)
+                float* gp = M.gpart + (size_t)(tk.kind >> 8) * M.sp * M.sp;
+                *reinterpret_cast<float4*>(gp + (int64_t)r * M.sp + c) = make_float4(v[0], v[1], v[2], v[3]);
+            } else if (kKind == kGram) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) v[j] *= s0 * s0;
                 *reinterpret_cast<float4*>(M.af + (int64_t)r * M.sp + c) = make_float4(v[0], v[1], v[2], v[3]);
@@ -172,7 +186,44 @@ __global__ void __launch_bounds__(256) simt_phase_kernel(const DevMat* __restric
     }
 }
 
+// A = s^2 sum_k P_k over one 128 x 128 tile (mat, tm, tn) of a split Gram:
+// partials summed in chunk order k = 0, 1, ..., the tile stored and, off the
+// diagonal, mirrored
+__global__ void __launch_bounds__(256) simt_gram_reduce_kernel(const DevMat* __restrict__ mats,
+                                                               const TileTask* __restrict__ tiles, int first,
+                                                               const float* __restrict__ nscale) {
+    const TileTask tk = tiles[blockIdx.x];
+    const DevMat& M = mats[tk.mat];
+    const float s0 = first ? nscale[tk.mat] : 1.f;
+    const size_t plane = (size_t)M.sp * M.sp;
+    for (int e = threadIdx.x; e < BM * (BN / 4); e += 256) {
+        const int r = tk.tm * BM + (e >> 5), c = tk.tn * BN + (e & 31) * 4;
+        const float* p = M.gpart + (int64_t)r * M.sp + c;
+        float4 acc = *reinterpret_cast<const float4*>(p);
+        for (int k = 1; k < M.ksplit; ++k) {
+            const float4 q = *reinterpret_cast<const float4*>(p + k * plane);
+            acc.x += q.x;
+            acc.y += q.y;
+            acc.z += q.z;
+            acc.w += q.w;
+        }
+        float v[4] = {acc.x * (s0 * s0), acc.y * (s0 * s0), acc.z * (s0 * s0), acc.w * (s0 * s0)};
+        *reinterpret_cast<float4*>(M.af + (int64_t)r * M.sp + c) = make_float4(v[0], v[1], v[2], v[3]);
+        if (tk.tm != tk.tn) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) M.af[(int64_t)(c + j) * M.sp + r] = v[j];
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_simt_gram_reduce(const DevMat* mats, const TileTask* tiles, int ntiles, int first,
+                                    const float* nscale, cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+    simt_gram_reduce_kernel<<<ntiles, 256, 0, st>>>(mats, tiles, first, nscale);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_simt_phase(const DevMat* mats, const TileTask* tiles, int ntiles, int kind,
                               float a, float b, float c, int src, int last, int first,

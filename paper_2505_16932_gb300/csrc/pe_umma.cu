@@ -149,18 +149,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// Multicast load: the box lands at the same shared-memory offset in every CTA
-// of `mask` (within the cluster) and completes bytes on each one's mbarrier at
-// the same offset.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
-                                               uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
-        : "memory");
-}
-
 // shared::cluster address of the same offset in CTA `rank` of the cluster
 __device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank) {
     uint32_t r;
@@ -259,29 +247,24 @@ __device__ __forceinline__ void umma_bf16_cg2(uint32_t d_tmem, uint64_t a_desc, 
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ void umma_commit_cg2_mc(uint64_t* bar, uint16_t mask) {
-    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                     smem_u32(bar)),
-                 "h"(mask)
+// 2-SM commit: one arrival on the mbarrier at the shared::cluster address
+// `bar_cluster` (this CTA's or the peer's) once every MMA issued so far by this
+// thread has completed
+__device__ __forceinline__ void umma_commit_cg2(uint32_t bar_cluster) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_cluster)
                  : "memory");
 }
 
-__device__ __forceinline__ void umma_commit_cg2(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+// the same barrier in both CTAs of the pair: one plain commit per CTA
+__device__ __forceinline__ void umma_commit_cg2_pair(uint64_t* bar) {
+    const uint32_t own = smem_u32(bar);
+    umma_commit_cg2(own);
+    umma_commit_cg2(mapa_rank(own, 1));
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
-                 : "memory");
-}
-
-// commit that arrives on the barrier at the same offset in every CTA of `mask`
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                     smem_u32(bar)),
-                 "h"(mask)
                  : "memory");
 }
 
@@ -345,11 +328,8 @@ __device__ void wait_counter(const int* cnt, int target, uint64_t limit, int* st
 
 // ------------------------------------------------------------ tile geometry
 
-// TileTask::kind carries the product in its low bits; kDummyBit marks the
-// idle member of a cluster pair (it loads its half of the shared operand for
-// its partner, computes and stores nothing).
+// TileTask::kind carries the product in its low bits.
 constexpr int kKindMask = 3;
-constexpr int kDummyBit = 0x100;
 
 struct Geo {
     int kind, mat, tm, tn, bn, nkb;
@@ -457,6 +437,37 @@ __device__ __forceinline__ void read_x_row(const uint8_t* buf, int r, float (&v)
             v[j + 1] = x_join(w[m] & 0xFFFF0000u, cw[(j + 1) >> 2], (j + 1) & 3);
         }
     }
+}
+
+// X - X_b for a decoded compact master x: its BF16 part X_b is
+// (bits(x) + 0x8000) with the low half cleared (the code adds at most
+// 0xFF00 - 0x8000 to hi << 16 and subtracts at most 0x8000), and the
+// difference of the two is exact
+__device__ __forceinline__ float x_lo(float x) {
+    return x - __uint_as_float((__float_as_uint(x) + 0x8000u) & 0xFFFF0000u);
+}
+
+// The BF16 update X' = a X + B X_b + d (X - X_b), X the compact master and
+// X_b its BF16 part (the MMA operand): in exact arithmetic this is a X + B X
+// for every d, and its rounding term is -(B - d I)(X - X_b). With d = 0 (the
+// plain a X + B X_b) that term does not vanish once the singular values
+// converge and B -> (1 - a) I, and the directions it rotates stay rotated;
+// d = tr(B) / s gives the term its smallest Frobenius norm, but early on it
+// hurts the small singular directions, whose later growth amplifies it. So
+// d = tr(B) / s once the mean of sigma^2, tr(A) / s, exceeds
+// kConvergedMeanSq, else d = 0.
+constexpr float kConvergedMeanSq = 0.8f;
+
+// sum over the warp of each lane's element v[lane] (the diagonal of a
+// diagonal chunk); every lane gets the same bits (xor butterfly)
+__device__ __forceinline__ float warp_diag_sum(const float (&v)[32], int lane) {
+    float d = 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+        if (j == lane) d = v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    return d;
 }
 
 // a row of X as hi (BF16 box at s_h) and code (box at s_q)
@@ -609,9 +620,9 @@ __device__ __forceinline__ void chunk_hl(const Geo& g, const DevMat& M, const St
 
 // -------------------------------------------------------------- kernel
 
-// MODE 0: one CTA per 128 x 256 tile. MODE 1: cluster pair sharing B by
-// multicast. MODE 2: 2-SM UMMA (cta_group::2) on 256 x 256 tiles, each CTA
-// holding half of A (its 128 rows) and half of B (128 of the 256 columns).
+// MODE 0: one CTA per 128 x 256 tile. MODE 2: 2-SM UMMA (cta_group::2) on
+// 256 x 256 tiles, each CTA holding half of A (its 128 rows) and half of B
+// (128 of the 256 columns). (MODE 1 is not used.)
 template <int NS, int BK, int MODE = 0>
 struct Cfg {
     static constexpr int kABytes = kBM * BK * 2;      // A tile of one k-block
@@ -642,11 +653,6 @@ enum ProfSlot {
     kPApRead = 13, kPApPf = 14, kPApMath = 15, kPApStore = 10, kPApFence = 16, kPApIssue = 17, kPApTmem = 18
 };
 
-// MC = 1: clusters of two CTAs run a pair of tiles that share the B operand
-// (same matrix, product and tile column; adjacent 128-row blocks). Each CTA
-// loads its own A and half of B, multicasting the half to both CTAs, so each
-// SM pulls 32 KB per k-block instead of 48 KB; a stage is free once both
-// CTAs' MMAs have consumed it (both commit to both CTAs' empty barriers).
 // MODE = 2: clusters of two CTAs run one 256 x 256 tile with 2-SM UMMA; the
 // even CTA issues the MMAs (M = 256), each CTA loads its half of A and B and
 // reads its 128 accumulator rows from its own TMEM. NACC accumulators of 256
@@ -656,7 +662,7 @@ enum ProfSlot {
 template <int NS, int BK, int MODE, int NACC, bool GF32 = false>
 __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_constant__ StepArgs A) {
     using C = Cfg<NS, BK, MODE>;
-    constexpr bool MC = (MODE == 1);
+    static_assert(MODE == 0 || MODE == 2, "kernel modes: 0 (1-SM tiles) and 2 (2-SM UMMA)");
     constexpr bool kCg2 = (MODE == 2);
     constexpr int kCols = 256 * NACC;
     constexpr int kABytes = C::kABytes;
@@ -679,15 +685,15 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
     const int unit = (MODE != 0) ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
     const int t_begin = A.off[unit];
     int t_end = A.off[unit + 1];
-    // tile `it` of this CTA: pairs are stored member 0, member 1
-#define PE_TILE(it) (A.tiles[MC ? 2 * (it) + crank : (it)])   // 2-SM: both CTAs read one entry
+    // tile `it` of this CTA (2-SM: both CTAs of the pair read the same entry)
+#define PE_TILE(it) (A.tiles[(it)])
     long long* prof = A.prof ? A.prof + 32 * blockIdx.x : nullptr;
     const long long k_t0 = clock64();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], MC ? 2 : 1);
+            mbar_init(&empty[s], 1);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&tfull[s], 1);
@@ -783,27 +789,13 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                     const uint32_t b_dst = sbase + C::kAOps * kABytes + o * kBBytes;
                     tma_load_2d(a_dst, mp + g.mapA + lo_off, &full[stage], kx, g.ya);
                     if (g.kind == kApply) {
-                        for (int j = 0; j < g.bn / 64; ++j) {
-                            if (MC) {
-                                if ((j & 1) == crank)
-                                    tma_load_2d_mc(b_dst + j * (64 * BK * 2), mp + g.mapB + lo_off, &full[stage],
-                                                   g.b0 + j * 64, kx, (uint16_t)3);
-                            } else {
-                                tma_load_2d(b_dst + j * (64 * BK * 2), mp + g.mapB + lo_off, &full[stage],
-                                            g.b0 + j * 64, kx);
-                            }
-                        }
+                        for (int j = 0; j < g.bn / 64; ++j)
+                            tma_load_2d(b_dst + j * (64 * BK * 2), mp + g.mapB + lo_off, &full[stage],
+                                        g.b0 + j * 64, kx);
                     } else {
-                        for (int h = 0; h < g.bn / kBM; ++h) {
-                            if (MC) {
-                                if ((h & 1) == crank)
-                                    tma_load_2d_mc(b_dst + h * kABytes, mp + g.mapB + lo_off, &full[stage], kx,
-                                                   g.b0 + h * kBM, (uint16_t)3);
-                            } else {
-                                tma_load_2d(b_dst + h * kABytes, mp + g.mapB + lo_off, &full[stage], kx,
-                                            g.b0 + h * kBM);
-                            }
-                        }
+                        for (int h = 0; h < g.bn / kBM; ++h)
+                            tma_load_2d(b_dst + h * kABytes, mp + g.mapB + lo_off, &full[stage], kx,
+                                        g.b0 + h * kBM);
                     }
                 }
                 issued |= 1u << stage;
@@ -868,20 +860,19 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                         else umma_bf16(d_tmem, adesc, bdesc, idesc, (kb | kk | p) != 0);
                     }
                 }
-                if (kCg2) umma_commit_cg2_mc(&empty[stage], (uint16_t)3);
-                else if (MC) umma_commit_mc(&empty[stage], (uint16_t)3);
+                if (kCg2) umma_commit_cg2_pair(&empty[stage]);
                 else umma_commit(&empty[stage]);
                 if (++stage == NST) { stage = 0; phase ^= 1; }
             }
             if (!ok) break;
-            if (kCg2) umma_commit_cg2_mc(&tfull[acc], (uint16_t)3);
+            if (kCg2) umma_commit_cg2_pair(&tfull[acc]);
             else umma_commit(&tfull[acc]);
             if (++acc == NACC) { acc = 0; acc_phase ^= 1; }
         }
         if (!ok) {
             *abort_flag = 1;
             atomicOr(A.status, 4);
-            if (kCg2) umma_commit_cg2(drain);
+            if (kCg2) umma_commit_cg2(smem_u32(drain));
             else umma_commit(drain);
             mbar_wait(drain, 0, limit, nullptr);
         }
@@ -915,19 +906,6 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             const DevMat& M = A.mats[tk.mat];
             const Geo g = tile_geo<BK>(tk, M, A.cur);
             const CUtensorMap* mp = A.maps + (size_t)tk.mat * kMapsPerMat;
-            if (MC && (tk.kind & kDummyBit)) {
-                // idle pair member: keep the accumulator hand-off, store nothing
-                if (!mbar_wait(&tfull[acc], acc_phase, limit, abort_flag)) {
-                    *abort_flag = 1;
-                    atomicOr(A.status, 4);
-                    break;
-                }
-                tc_fence_after();
-                tc_fence_before();
-                mbar_arrive(&tempty[acc]);
-                if (++acc == NACC) { acc = 0; acc_phase ^= 1; }
-                continue;
-            }
             // the warp's first row (2-SM: this CTA holds rows 128 crank .. of the 256-row tile)
             const int gi0 = (kCg2 ? tk.tm * 2 * kBM + crank * kBM : g.tm * kBM) + q * 32;
             const int gi = gi0 + lane;
@@ -992,6 +970,37 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             const long long c1 = clock64();
             c_tfull += c1 - c0;
             const uint32_t tbase = tmem_base + acc * 256 + ((uint32_t)(q * 32) << 16) + grp * nch * 32;
+            // BF16 update: d of the update (see kConvergedMeanSq) from the
+            // parts of tr(B) and tr(A) the square and Gram epilogues left per
+            // 32-row diagonal chunk, each summed in a fixed order (lane k takes
+            // parts k, k + 32, ..., then a butterfly); the parts of a pack's
+            // 64-row block k are 2k and 2k + 1
+            float dtr = 0.f;
+            if (NS == 1 && g.kind == kApply && M.btr) {
+                if (A.dependent) {   // the parts come from other CTAs: acquire their releases
+                    const int which = A.cubic ? 0 : 1;
+                    const int* cnt = A.counters + 2 * g.mat + which;
+                    if (lane == 0) wait_counter(cnt, (A.step + 1) * A.need[2 * g.mat + which], limit, A.status);
+                    __syncwarp();
+                    (void)ld_acquire(cnt);
+                    (void)ld_acquire(A.counters + 2 * g.mat);   // the Gram's (tr(A) parts)
+                }
+                const int nsl = M.npack ? 2 : M.sp / 32;
+                const float* slb = M.btr + (M.npack ? 2 * (gi0 >> 6) : 0);
+                const float* sla = slb + M.sp / 32;
+                float tb = 0.f, ta = 0.f;
+                for (int k = lane; k < nsl; k += 32) {
+                    tb += __ldcg(slb + k);
+                    ta += __ldcg(sla + k);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    tb += __shfl_xor_sync(0xffffffffu, tb, o);
+                    ta += __shfl_xor_sync(0xffffffffu, ta, o);
+                }
+                if (A.cubic) ta = (A.b != 0.f) ? tb / A.b : 0.f;   // B = b A
+                if (ta > kConvergedMeanSq * (float)M.s) dtr = tb / (float)M.s;
+            }
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 if (i >= nch || i < first) continue;
@@ -1029,21 +1038,30 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                         }
                     }
                     if (g.kind == kApply) {
+                        // X' = a X + B X_b + d (X - X_b) (see x_lo)
                         if (A.step == 0) {
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) v[j] = s0 * fmaf(A.a, pre[j], v[j]);
+                            for (int j = 0; j < 32; ++j) v[j] = s0 * fmaf(dtr, x_lo(pre[j]), fmaf(A.a, pre[j], v[j]));
                         } else {
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) v[j] = fmaf(A.a, pre[j], v[j]);
+                            for (int j = 0; j < 32; ++j) v[j] = fmaf(dtr, x_lo(pre[j]), fmaf(A.a, pre[j], v[j]));
                         }
                     } else if (g.kind == kSquare) {
 #pragma unroll
                         for (int j = 0; j < 32; ++j) v[j] = fmaf(A.b, pre[j], A.c * v[j]);
+                        if (M.btr && cls == kChunkDiag) {
+                            const float dg = warp_diag_sum(v, lane);
+                            if (lane == 0) M.btr[gi0 >> 5] = dg;
+                        }
                     } else {
                         // Gram: A = s^2 X X^T, or B = b s^2 X X^T when c = 0 throughout
                         const float gs = A.cubic ? A.b * s0 * s0 : s0 * s0;
 #pragma unroll
                         for (int j = 0; j < 32; ++j) v[j] *= gs;
+                        if (M.btr && cls == kChunkDiag) {   // tr(B) parts (c = 0), else tr(A) parts
+                            const float dg = warp_diag_sum(v, lane);
+                            if (lane == 0) M.btr[(A.cubic ? 0 : M.sp / 32) + (gi0 >> 5)] = dg;
+                        }
                     }
                     if (sub) { const long long t = clock64(); c_rdx += t - s0c; s0c = t; }
                     if (GF32 && g.kind == kGram) {
@@ -1300,62 +1318,24 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // tiles (memory-heavy) of early matrices run beside Gram tiles
 // (compute-heavy) of later ones. Every order lists a matrix's phases in
 // dependency order, which is what the readiness waits need for progress.
-//
-// With cluster multicast (mc), the scheduling units are pairs of tiles that
-// share the B operand (same matrix, product, tile column; row blocks 2p and
-// 2p+1); a missing member becomes an idle copy of its partner.
+
 namespace {
 
 struct Unit {
-    TileTask t[2];   // member 0, member 1 (t[1] unused without multicast)
+    TileTask t;
     double cost;
 };
 
-std::vector<Unit> make_units(const std::vector<TileTask>& tiles, const std::vector<double>& cost, bool mc) {
+std::vector<Unit> make_units(const std::vector<TileTask>& tiles, const std::vector<double>& cost) {
     std::vector<Unit> u;
-    if (!mc) {
-        for (size_t i = 0; i < tiles.size(); ++i) u.push_back(Unit{{tiles[i], tiles[i]}, cost[i]});
-        return u;
-    }
-    // group by (matrix, tile column, row pair)
-    std::vector<size_t> idx(tiles.size());
-    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
-    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
-        const TileTask &x = tiles[a], &y = tiles[b];
-        if (x.mat != y.mat) return x.mat < y.mat;
-        if (x.tn != y.tn) return x.tn < y.tn;
-        return x.tm < y.tm;
-    });
-    for (size_t k = 0; k < idx.size();) {
-        const TileTask& a = tiles[idx[k]];
-        double c = cost[idx[k]];
-        Unit v;
-        if (k + 1 < idx.size()) {
-            const TileTask& b = tiles[idx[k + 1]];
-            if (b.mat == a.mat && b.tn == a.tn && (a.tm & 1) == 0 && b.tm == a.tm + 1) {
-                v.t[0] = a;
-                v.t[1] = b;
-                v.cost = std::max(c, cost[idx[k + 1]]);
-                u.push_back(v);
-                k += 2;
-                continue;
-            }
-        }
-        TileTask d = a;
-        d.kind |= kDummyBit;
-        if (a.tm & 1) { v.t[0] = d; v.t[1] = a; }
-        else { v.t[0] = a; v.t[1] = d; }
-        v.cost = c;
-        u.push_back(v);
-        k += 1;
-    }
+    for (size_t i = 0; i < tiles.size(); ++i) u.push_back(Unit{tiles[i], cost[i]});
     return u;
 }
 
 void sort_units(std::vector<Unit>& v, int mode, const std::vector<double>& mat_cost) {
     std::vector<HostTile> h;
     for (size_t i = 0; i < v.size(); ++i) {
-        TileTask key = v[i].t[(v[i].t[0].kind & kDummyBit) ? 1 : 0];
+        TileTask key = v[i].t;
         key.kind = (int)i;   // carry the unit index through the sort
         h.push_back(HostTile{key, v[i].cost});
     }
@@ -1365,7 +1345,7 @@ void sort_units(std::vector<Unit>& v, int mode, const std::vector<double>& mat_c
     v.swap(out);
 }
 
-void lpt_units(const std::vector<Unit>& order, int groups, std::vector<int>* off, std::vector<TileTask>* out, bool mc) {
+void lpt_units(const std::vector<Unit>& order, int groups, std::vector<int>* off, std::vector<TileTask>* out) {
     std::vector<std::vector<int>> per(groups);
     typedef std::pair<double, int> Load;
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
@@ -1383,8 +1363,7 @@ void lpt_units(const std::vector<Unit>& order, int groups, std::vector<int>* off
     for (int c = 0; c < groups; ++c) {
         (*off)[c] = n;
         for (int i : per[c]) {
-            out->push_back(order[i].t[0]);
-            if (mc) out->push_back(order[i].t[1]);
+            out->push_back(order[i].t);
             ++n;
         }
     }
@@ -1394,13 +1373,12 @@ void lpt_units(const std::vector<Unit>& order, int groups, std::vector<int>* off
 }  // namespace
 
 int umma_schedule(UmmaPlan* P, int order, std::string* err) {
-    const bool mc = P->mode == 1;      // pairs of tiles (two list entries per unit)
-    const bool cg2 = P->mode == 2;     // one 256 x 256 tile per unit, one entry
+    const bool cg2 = P->mode == 2;     // one 256 x 256 tile per unit
     const int inphase = (order == 1) ? 1 : 0;
     std::vector<Unit> ph[3];
     for (int k = 0; k < 3; ++k) {
-        if (cg2) ph[k] = make_units(P->ph2_t[k], P->ph2_c[k], false);
-        else ph[k] = make_units(P->ph_t[k], P->ph_c[k], mc);
+        if (cg2) ph[k] = make_units(P->ph2_t[k], P->ph2_c[k]);
+        else ph[k] = make_units(P->ph_t[k], P->ph_c[k]);
         sort_units(ph[k], inphase, P->mat_cost);
     }
     std::vector<Unit> fused;
@@ -1417,7 +1395,7 @@ int umma_schedule(UmmaPlan* P, int order, std::string* err) {
         std::vector<Keyed> all;
         for (int k = 0; k < 3; ++k)
             for (size_t i = 0; i < ph[k].size(); ++i)
-                all.push_back(Keyed{(long)rank[ph[k][i].t[0].mat] + (long)lag * k, k, i});
+                all.push_back(Keyed{(long)rank[ph[k][i].t.mat] + (long)lag * k, k, i});
         std::stable_sort(all.begin(), all.end(), [](const Keyed& a, const Keyed& b) {
             if (a.key != b.key) return a.key < b.key;
             if (a.phase != b.phase) return a.phase < b.phase;
@@ -1425,21 +1403,21 @@ int umma_schedule(UmmaPlan* P, int order, std::string* err) {
         });
         for (const Keyed& k : all) fused.push_back(ph[k.phase][k.pos]);
     }
-    const int cap = mc ? P->max_clusters : cg2 ? P->max_clusters2 : P->sms;   // scheduling groups
+    const int cap = cg2 ? P->max_clusters2 : P->sms;   // scheduling groups
     P->ntiles = (int)fused.size();
     const int groups = std::max(1, std::min(cap, P->ntiles));
-    P->grid = (mc || cg2) ? 2 * groups : groups;
+    P->grid = cg2 ? 2 * groups : groups;
     std::vector<int> off;
     std::vector<TileTask> list;
-    lpt_units(fused, groups, &off, &list, mc);
+    lpt_units(fused, groups, &off, &list);
     cudaError_t e = cudaMemcpy(P->tiles, list.data(), sizeof(TileTask) * list.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->tile_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
         std::vector<int> poff;
         std::vector<TileTask> plist;
         const int g = std::max(1, std::min(cap, (int)ph[k].size()));
-        lpt_units(ph[k], g, &poff, &plist, mc);
-        P->grid_phase[k] = ph[k].empty() ? 0 : ((mc || cg2) ? 2 * g : g);
+        lpt_units(ph[k], g, &poff, &plist);
+        P->grid_phase[k] = ph[k].empty() ? 0 : (cg2 ? 2 * g : g);
         if (!plist.empty())
             e = cudaMemcpy(P->ph_tiles[k], plist.data(), sizeof(TileTask) * plist.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(P->ph_off[k], poff.data(), sizeof(int) * poff.size(), cudaMemcpyHostToDevice);
@@ -1462,7 +1440,7 @@ size_t umma_workspace_bytes(const DevMat* mats, int count) {
     }
     size_t b = 0;
     b += align_up(sizeof(CUtensorMap) * kMapsPerMat * count, 1024);
-    b += 2 * align_up(sizeof(TileTask) * (2 * tiles + 2), 256);   // fused + phased lists (pairs: 2 per unit)
+    b += 2 * align_up(sizeof(TileTask) * (tiles + 2), 256);   // fused + phased lists
     b += 4 * align_up(sizeof(int) * (4096 + 1), 256);         // CSR offsets (grid <= 4096)
     b += 2 * align_up(sizeof(int) * 2 * count, 256);
     return b + 4096;
@@ -1514,12 +1492,17 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
             *err = "cuTensorMapEncodeTiled failed for matrix " + std::to_string(i);
             return PE_ECUDA;
         }
-        // the caller's buffer takes TMA stores when it is 16-byte aligned with
-        // a 16-byte multiple pitch
+        // the caller's buffer takes TMA stores when it is 16-byte aligned, its
+        // pitch is a multiple of 16 bytes and so is its row (n elements): a
+        // box that crosses the right edge of the tensor is written in whole
+        // 16-byte granules, so a row ending inside a granule would get the
+        // padding columns' zeros written past its end (into the caller's gap
+        // between rows); such matrices take element-wise stores (out_user)
         const int esz = (M.io == PE_IO_BF16) ? 2 : 4;
         M.out_tma = 0;
         void* out = M.w ? (void*)M.w : M.user;   // fused Muon step: the box is reduce-added into W
-        if (P->nsplit == 1 && !M.npack && reinterpret_cast<uintptr_t>(out) % 16 == 0 && (M.ld * esz) % 16 == 0) {
+        if (P->nsplit == 1 && !M.npack && reinterpret_cast<uintptr_t>(out) % 16 == 0 && (M.ld * esz) % 16 == 0 &&
+            ((int64_t)M.n * esz) % 16 == 0) {
             M.out_tma = make_map(enc, mp + kMapEOut, out, M.m, M.n, M.ld * esz, 32, 32, esz == 4 ? F32 : BF,
                                  esz == 4 ? S128 : S64)
                             ? 1
@@ -1551,16 +1534,16 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
     char* base = ws;
     auto take = [&](size_t bytes, size_t al) { o = align_up(o, al); char* p = base + o; o += bytes; return p; };
     P->maps = take(sizeof(CUtensorMap) * maps.size(), 1024);
-    P->tiles = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (2 * ntot + 2), 256));
+    P->tiles = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (ntot + 2), 256));
     P->tile_off = reinterpret_cast<int*>(take(sizeof(int) * (sms + 1), 256));
     P->need = reinterpret_cast<int*>(take(sizeof(int) * 2 * count, 256));
     P->need2 = reinterpret_cast<int*>(take(sizeof(int) * 2 * count, 256));
-    TileTask* ph_base = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (2 * ntot + 2), 256));
+    TileTask* ph_base = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (ntot + 2), 256));
     size_t ph_pos = 0;
     for (int k = 0; k < 3; ++k) {
         P->ph_tiles[k] = ph_base + ph_pos;
         P->ph_off[k] = reinterpret_cast<int*>(take(sizeof(int) * (sms + 1), 256));
-        ph_pos += 2 * ph[k].size();
+        ph_pos += ph[k].size();
     }
     if (o > ws_bytes) {
         *err = "internal: tcgen05 workspace too small";
@@ -1580,9 +1563,6 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(umma_step_kernel<1, 32, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Cfg<1, 32>::kSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(umma_step_kernel<1, 64, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)Cfg<1, 64>::kSmem);
     if (e == cudaSuccess && P->gram_f32)
         e = cudaFuncSetAttribute(umma_step_kernel<1, 64, 0, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Cfg<1, 64>::kSmem);
@@ -1595,26 +1575,6 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
     if (e != cudaSuccess) {
         *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
         return PE_ECUDA;
-    }
-    // clusters of two CTAs that can be resident at once (multicast variant)
-    P->max_clusters = 0;
-    if (P->nsplit == 1 && P->bk == 64) {   // multicast pairs
-        cudaLaunchConfig_t cfg;
-        memset(&cfg, 0, sizeof(cfg));
-        cfg.gridDim = dim3(2 * (sms / 2));
-        cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = Cfg<1, 64>::kSmem;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, umma_step_kernel<1, 64, 1, 2>, &cfg) == cudaSuccess)
-            P->max_clusters = std::min(n, sms / 2);
-        cudaGetLastError();
     }
     // 2-SM UMMA: 256 x 256 tiles, needs every padded size to be a multiple of 256
     P->max_clusters2 = 0;
@@ -1672,7 +1632,7 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
         }
         cudaGetLastError();
     }
-    if (P->mode == 1 && P->max_clusters < 1) P->mode = 0;
+    if (P->mode != 0 && P->mode != 2) P->mode = 0;
     if (P->mode == 2 && P->max_clusters2 < 1) P->mode = 0;
     return umma_schedule(P, P->order, err);
 }
@@ -1707,8 +1667,8 @@ cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, i
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         if (P->mode != 0) {
-            // clusters of two; co-residency of the whole grid comes from sizing
-            // it by cudaOccupancyMaxActiveClusters at plan time
+            // 2-SM pairs; co-residency of the whole grid comes from sizing it
+            // by cudaOccupancyMaxActiveClusters at plan time
             attr[0].id = cudaLaunchAttributeClusterDimension;
             attr[0].val.clusterDim.x = 2;
             attr[0].val.clusterDim.y = 1;
@@ -1729,7 +1689,6 @@ cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, i
             if (P->nacc == 2) return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64, 2, 2>, A);
             return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64, 2, 1>, A);
         }
-        if (P->mode == 1) return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64, 1, 2>, A);
         if (P->bk == 64) return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64, 0, 2>, A);
         return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 32, 0, 2>, A);
     };

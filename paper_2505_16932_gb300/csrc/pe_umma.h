@@ -31,14 +31,13 @@ struct UmmaPlan {
     int apply_bn = 256;
     int bk = 64;             // k-block of the tcgen05 kernel (64 or 32)
     int order = 0;           // tile order (see umma_schedule)
-    int mode = 0;            // 0 one CTA per 128x256 tile; 1 cluster pairs sharing B by TMA
-                             // multicast; 2 2-SM UMMA (cta_group::2) on 256x256 tiles
+    int mode = 0;            // 0 one CTA per 128x256 tile; 2 2-SM UMMA (cta_group::2) on
+                             // 256x256 tiles
     int nacc = 2;            // accumulators per CTA in mode 2 (1 or 2)
     bool cubic = false;      // every step has c = 0 (BF16 only): B = b A comes from the
                              // Gram epilogue and there are no square tiles
     bool gram_f32 = false;   // long-side split: the Gram writes the full FP32 A into DevMat::af
                              // (its own kernel instantiation; mode 0, 64-wide k-blocks)
-    int max_clusters = 0;    // co-resident clusters of two, multicast kernel (0: unavailable)
     int max_clusters2 = 0;   // co-resident clusters of two, 2-SM kernel (0: unavailable)
     size_t smem_bytes2 = 0;  // dynamic shared memory of the 2-SM kernel
     int* need2 = nullptr;    // device: per matrix readiness targets of 2-SM plans

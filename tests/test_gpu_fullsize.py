@@ -164,10 +164,10 @@ def test_newton_schulz_table_through_same_kernels():
         assert O.rel_fro(X.cpu().numpy().astype(np.float64), ref) <= tol
 
 
-# FP32 accumulation of a length-K dot product errs by about sqrt(K) u
-# (u = 2^-24) when rounding errors are random; with K = 2^20 the plain
-# method cannot reach 1e-5, so its bar here is 16 sqrt(K) u ~ 1e-3.
-@pytest.mark.parametrize("path,tol", [("fp32", 16 * 2.0 ** 10 * 2.0 ** -24), ("bf16", 2e-2)])
+# The stated bars (FP32 1e-5, BF16 2e-2) on the longest supported vector:
+# the FP32 Gram's reduction of length 2^20 runs as 256 chunks of 4096 summed
+# in chunk order, so no accumulator sums more than 4096 products.
+@pytest.mark.parametrize("path,tol", [("fp32", 1e-5), ("bf16", 2e-2)])
 def test_longest_vector(path, tol):
     n = 1 << 20
     v = np.random.default_rng(1).standard_normal((1, n))

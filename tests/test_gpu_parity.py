@@ -116,11 +116,14 @@ def test_single_products(dtype, m, n, row):
         X0 = X0.T
     a, b, c = row
     if dtype == "bf16":
+        # the BF16 update a X + B X_b + d (X - X_b), d = tr(B) / s
         Xh = bf16r(X0)
         A = Xh @ Xh.T
         Ah = bf16r(A)
-        Bm = bf16r(b * A + c * (Ah @ Ah))
-        ref = a * X0 + Bm @ Xh
+        Bf = b * A + c * (Ah @ Ah)
+        Bm = bf16r(Bf)
+        d = np.trace(Bf) / min(m, n)
+        ref = a * X0 + Bm @ Xh + d * (X0 - Xh)
         tol = 1e-2
     else:
         A = X0 @ X0.T
@@ -234,21 +237,14 @@ def test_graph_replay_repeats():
         assert torch.equal(X, F)
 
 
-# BF16 on iid Gaussian inputs run well past convergence: the a X term uses
-# the 16-bit-mantissa master while B X uses its BF16 rounding X_b, so each
-# converged step adds -B (X - X_b) ~ (a_t - 1) 2^-9 / sqrt(3) |X| of rotation
-# error that later steps do not damp; with the T = 6, l = 1e-3 table this sums
-# to ~2.4e-2 on such inputs (2.39e-2 measured in a CPU emulation of the same
-# arithmetic), against 4-5e-3 on the heavy-tailed spectra of the Muon
-# workloads. The bar for this case is that bound rounded up; BF16x3, whose
-# update is compensated, keeps the 2e-2 bar.
-BF16_TOL_GAUSS_CONVERGED = 3e-2
-
-
 def test_batched_vs_oracle_uneven():
     mats = _uneven(seed=9)
     tab = table(1e-3, 6)
-    for dtype, tol in (("fp32", FP32_TOL), ("bf16", BF16_TOL_GAUSS_CONVERGED), ("bf16x3", BF16_TOL)):
+    # iid Gaussian inputs iterated well past their convergence: the BF16
+    # update's rounding term is -(B - d I)(X - X_b), d = tr(B) / s, which
+    # vanishes on converged directions (the stated 2e-2 bar holds; the plain
+    # a X + B X_b form reached 2.4e-2 here)
+    for dtype, tol in (("fp32", FP32_TOL), ("bf16", BF16_TOL), ("bf16x3", BF16_TOL)):
         Xs = [to_dev(G) for G in mats]
         pe.pe_polar_batched(Xs, tab, dtype)
         pe.pe_sync_status()
@@ -342,22 +338,20 @@ def test_empty_and_bad_shapes_rejected():
 
 @pytest.mark.parametrize("dtype", ["bf16", "bf16x3"])
 def test_kblock_and_order_variants_bitwise(dtype):
-    """The 32-wide k-block variant, the tile orders, the cluster-multicast
-    variant and the 2-SM variant issue the same K=16 MMA chain on the same
-    operands per output element, so every variant gives identical bits (the
-    2-SM mode needs every padded size to be a multiple of 256; the shapes
-    that are not fall back to the 1-SM kernel)."""
+    """The 32-wide k-block variant, the tile orders and the 2-SM variant
+    issue the same K=16 MMA chain on the same operands per output element, so
+    every variant gives identical bits (the 2-SM mode needs every padded size
+    to be a multiple of 256; the shapes that are not fall back to the 1-SM
+    kernel)."""
     mats = _uneven(seed=21)
     tab = table(1e-3, 4)
     outs = []
     try:
-        for bk, order, mc in ((64, 0, 0), (32, 0, 0), (64, 1, 0), (32, 1, 0), (64, 2, 0), (64, 4, 0),
-                              (64, 0, 1), (64, 1, 1), (64, 3, 1), (64, 0, 2), (64, 4, 2)):
-            if mc and dtype != "bf16":
-                continue
+        for bk, order, mode in ((64, 0, 0), (32, 0, 0), (64, 1, 0), (32, 1, 0), (64, 2, 0), (64, 4, 0),
+                                (64, 3, 0), (64, 0, 2), (64, 1, 2), (64, 4, 2)):
             pe.pe_debug_set(5, bk)
             pe.pe_debug_set(6, order)
-            pe.pe_debug_set(7, mc)
+            pe.pe_debug_set(7, mode)
             pe.pe_release()
             Xs = [to_dev(G) for G in mats]
             pe.pe_polar_batched(Xs, tab, dtype)
