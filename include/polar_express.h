@@ -395,10 +395,12 @@ int pe_split_close(pe_split_t handle);
  * normalises) and f = ||X_0||_F: the power method (subspace iteration with
  * one vector) on X_0 X_0^T gives z <= sigma_1(X_0); the Frobenius identity
  * then bounds sigma_1 in [z, f] and every other singular value by
- * w = sqrt(f^2 - z^2). When 2 z^2 > f^2 the odd cubic p(x) = a x + b x^3 with
+ * w = sqrt(f^2 - z^2). When the intervals [0, w] and [z, f] are disjoint
+ * (2 z^2 > f^2, and z < f) the odd cubic p(x) = a x + b x^3 with
  * p(w) = p(z) = 1 (Eq. init_poly, as a polynomial of x / f) maps the spectrum
  * into [l', 1], l' = min(l / w, p(f)), and T Polar Express steps for [l', 1]
- * follow; otherwise T + 1 ordinary steps for [l, 1].
+ * follow; otherwise T + 1 ordinary steps for [l, 1] (the cubic counts as a
+ * step, as in the appendix's comparison).
  */
 
 /* Lower bound of sigma_1 by `iters` power steps v <- X_0 X_0^T v / ||.||
@@ -413,20 +415,38 @@ int pe_split_close(pe_split_t handle);
 int pe_spectrum_bound(const void* X, int64_t m, int64_t n, const float* v0, int iters, double* z, double* f,
                       void* stream);
 
+/* Option of pe_spectrum_aware_table_ex / pe_polar_spectrum_aware_ex (not in
+ * the appendix): keep the cubic only when the greedy lower bound (Thm. 1)
+ * of its composition after the last step exceeds that of the plain
+ * composition with T + 1 steps. */
+#define PE_SPECTRUM_GATE 1u
+
 /* Host: the coefficient table of the initialised iteration, T + 1 rows of
  * (a, b, c) into table (caller-owned, 3 (T + 1) doubles): row 0 the cubic
  * (a, b, 0) and rows 1..T the pe_coeffs(5, l', T, 1.01) composition, or, when
- * the cubic does not apply, pe_coeffs(5, l, T + 1, 1.01). z is shrunk by a
- * relative 1e-5 first (so that an FP32 evaluation of the bound cannot exceed
- * sigma_1 by rounding). info (nullable, 6 doubles): applied (1 or 0), the z
- * used, f, a, b, l'. T in 0..63, l in (0, 1]. Errors: PE_EINVAL, PE_ENOCONV. */
+ * the cubic does not apply, pe_coeffs(5, l, T + 1, 1.01). z is used as given.
+ * info (nullable, 6 doubles): applied (1 or 0), the z used, f, a, b, l'.
+ * T in 0..63, l in (0, 1]. Errors: PE_EINVAL, PE_ENOCONV. */
 int pe_spectrum_aware_table(double z, double f, double l, int T, double* table, double* info);
 
-/* pe_spectrum_bound, pe_spectrum_aware_table, then pe_polar with that table
- * (T + 1 steps) on X in place. X as for pe_polar (FP32, device, in/out);
- * dtype PE_FP32, PE_BF16 or PE_BF16X3; info as for pe_spectrum_aware_table.
- * Each call builds a plan for its data-dependent table (a cached tuned
- * schedule of the same shape is reused). Errors: as the three calls. */
+/* As pe_spectrum_aware_table, with z first shrunk to z (1 - z_safety),
+ * z_safety in [0, 1) (a caller whose z carries rounding error keeps it below
+ * sigma_1), and flags 0 or PE_SPECTRUM_GATE. */
+int pe_spectrum_aware_table_ex(double z, double f, double l, int T, double z_safety, unsigned flags, double* table,
+                               double* info);
+
+/* pe_spectrum_bound, pe_spectrum_aware_table_ex, then pe_polar with that
+ * table (T + 1 steps) on X in place. X as for pe_polar (FP32, device,
+ * in/out); dtype PE_FP32, PE_BF16 or PE_BF16X3; z_safety and flags as for
+ * pe_spectrum_aware_table_ex; info as for pe_spectrum_aware_table. Each call
+ * builds a plan for its data-dependent table (a cached tuned schedule of the
+ * same shape is reused). Errors: as the three calls. */
+int pe_polar_spectrum_aware_ex(void* X, int64_t m, int64_t n, double l, int T, int dtype, const float* v0, int iters,
+                               double z_safety, unsigned flags, double* info, void* stream);
+
+/* pe_polar_spectrum_aware_ex with z_safety = 1e-5 (the bound z is computed
+ * in FP32 on the GPU; the shrink keeps its rounding from lifting it above
+ * sigma_1) and flags 0 (the appendix's rule). */
 int pe_polar_spectrum_aware(void* X, int64_t m, int64_t n, double l, int T, int dtype, const float* v0, int iters,
                             double* info, void* stream);
 

@@ -15,25 +15,27 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
   p(w) = p(z) = 1 is the paper's Eq. init_poly, written there for f = 1; for
   another f it is the same polynomial of x / f (Eq. init_poly at z / f, then
   a / f and b / f^3).
-* ``spectrum_aware_table``: the cubic as a first row (a, b, 0) followed by the
-  Polar Express composition for the interval the cubic leaves, [l', 1] with
-  l' = min(l / w, p(f)): p lies above the chord x / w on [0, w] (concave and
-  increasing there), so the tail's lower bound l becomes l / w, and p is
-  decreasing on [z, f], so sigma_1 ends in [p(f), 1]. Of this table and the
-  plain composition with one more step, the one whose greedy lower bound after
-  the last step is larger is used.
+* ``spectrum_aware_table``: when the cubic applies, it is the first row
+  (a, b, 0), followed by the Polar Express composition for the interval the
+  cubic leaves, [l', 1] with l' = min(l / w, p(f)): p lies above the chord
+  x / w on [0, w] (concave and increasing there), so the tail's lower bound l
+  becomes l / w, and p is decreasing on [z, f], so sigma_1 ends in [p(f), 1].
+  Otherwise the table is the plain composition with T + 1 rows (the cubic
+  counts as an iteration, as in the appendix's comparison).
 * ``spectrum_aware_polar``: normalise (the online code's 1.01 ||G||_F + 1e-7),
   bound, table, then the ordinary iteration over that table (which treats the
   cubic row like any other: A = X X^T, B = b A, X = a X + B X).
 
 Readings (the appendix leaves these open): the power method runs on the
-normalised X_0; the relative safety ``z_safety`` (default 1e-5) shrinks z
-before use, so that an FP32 evaluation of the same bound on a GPU cannot
-exceed sigma_1 by rounding; the cubic is considered only when 2 z^2 > f^2
-(strictly disjoint intervals) and w > 0, and kept only when its final
-greedy bound beats that of the plain composition with one more step (the
-appendix says the scheme helps when there is a large outlying singular
-value; this makes "helps" the composition's own guarantee).
+normalised X_0; the cubic applies exactly when the appendix builds it, i.e.
+when the intervals [0, w] and [z, f] are disjoint, read strictly (2 z^2 > f^2:
+at equality Eq. init_poly divides by zero) and with w > 0 (z < f; at z = f it
+is singular too). Two options are not the paper's and are off by default:
+``z_safety`` shrinks z by a relative amount before use (a caller that
+evaluates the bound in FP32 can keep it below sigma_1 despite rounding), and
+``gate`` keeps the cubic only when the greedy lower bound its composition
+reaches after the last step beats that of the plain composition with one
+more step.
 """
 from __future__ import annotations
 
@@ -45,7 +47,7 @@ import numpy as np
 from .iteration import NORM_EPS, NORM_SCALE, normalise, polar_express
 from .minimax import optimal_composition
 
-Z_SAFETY = 1e-5
+Z_SAFETY = 0.0   # the paper uses z as computed
 
 
 def power_bound(X: np.ndarray, v0: Sequence[float], iters: int) -> float:
@@ -88,12 +90,12 @@ def init_cubic(z: float, f: float) -> Optional[Tuple[float, float, float]]:
 
 
 def spectrum_aware_table(z: float, f: float, l: float, T: int, safety: float = 1.01,
-                         z_safety: float = Z_SAFETY):
-    """(table, info): the cubic row plus T Polar Express rows for [l', 1], or
-    the plain composition with T + 1 rows when the cubic does not apply or
-    guarantees less: the cubic is kept only if the lower bound it leaves
+                         z_safety: float = Z_SAFETY, gate: bool = False):
+    """(table, info): the cubic row plus T Polar Express rows for [l', 1]
+    when the cubic applies (App. H), else the plain composition with T + 1
+    rows. With ``gate`` the cubic is kept only if the lower bound it leaves
     after its T steps, l'_T, exceeds the plain composition's l_{T+1} (the
-    greedy bounds of Thm. 1; the cubic pays off when z is close to f)."""
+    greedy bounds of Thm. 1)."""
     zs = z * (1.0 - z_safety)
     cub = init_cubic(zs, f)
     plain, pbounds = optimal_composition(l, T + 1, safety=safety)
@@ -108,7 +110,7 @@ def spectrum_aware_table(z: float, f: float, l: float, T: int, safety: float = 1
         else:
             rest, l_final = [], lp
         info.update({"w": w, "a": a, "b": b, "p_f": pf, "l_final_init": l_final})
-        if l_final > pbounds[-1][0]:
+        if not gate or l_final > pbounds[-1][0]:
             table: List[Tuple[float, float, float]] = [(a, b, 0.0)] + [tuple(r) for r in rest]
             info.update({"applied": True, "l_after": lp})
             return table, info
@@ -116,7 +118,7 @@ def spectrum_aware_table(z: float, f: float, l: float, T: int, safety: float = 1
 
 
 def spectrum_aware_polar(G: np.ndarray, l: float, T: int, v0: Sequence[float], iters: int,
-                         safety: float = 1.01, z_safety: float = Z_SAFETY):
+                         safety: float = 1.01, z_safety: float = Z_SAFETY, gate: bool = False):
     """App. H initialisation followed by T Polar Express steps; returns
     (X, table, info). X_0 is the s x L normalised matrix (short side first);
     the power method runs on the s x s matrix X_0 X_0^T, so v0 has
@@ -124,5 +126,5 @@ def spectrum_aware_polar(G: np.ndarray, l: float, T: int, v0: Sequence[float], i
     X0, _ = normalise(G, NORM_SCALE, NORM_EPS)
     f = float(np.linalg.norm(X0))
     z = power_bound(X0.T, v0, iters)
-    table, info = spectrum_aware_table(z, f, l, T, safety, z_safety)
+    table, info = spectrum_aware_table(z, f, l, T, safety, z_safety, gate)
     return polar_express(G, table), table, info

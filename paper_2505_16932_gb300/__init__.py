@@ -92,8 +92,11 @@ def lib() -> ctypes.CDLL:
         "pe_split_close": (c_i, [c_p]),
         "pe_spectrum_bound": (c_i, [c_p, c_i64, c_i64, ctypes.POINTER(ctypes.c_float), c_i, P_d, P_d, c_p]),
         "pe_spectrum_aware_table": (c_i, [c_d, c_d, c_d, c_i, P_d, P_d]),
+        "pe_spectrum_aware_table_ex": (c_i, [c_d, c_d, c_d, c_i, c_d, c_u, P_d, P_d]),
         "pe_polar_spectrum_aware": (c_i, [c_p, c_i64, c_i64, c_d, c_i, c_i, ctypes.POINTER(ctypes.c_float), c_i,
                                           P_d, c_p]),
+        "pe_polar_spectrum_aware_ex": (c_i, [c_p, c_i64, c_i64, c_d, c_i, c_i, ctypes.POINTER(ctypes.c_float), c_i,
+                                             c_d, c_u, P_d, c_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -215,25 +218,37 @@ def pe_spectrum_bound(X, v0, iters: int = 10, stream=None):
     return z.value, f.value
 
 
-def pe_spectrum_aware_table(z: float, f: float, l: float, T: int):
-    """(table (T + 1, 3), info) of the initialised iteration (host)."""
+PE_SPECTRUM_GATE = 1
+
+
+def pe_spectrum_aware_table(z: float, f: float, l: float, T: int, z_safety: float = 0.0, gate: bool = False):
+    """(table (T + 1, 3), info) of the initialised iteration (host); the
+    appendix's rule unless ``gate`` (PE_SPECTRUM_GATE) or ``z_safety``."""
     tab = np.zeros((T + 1, 3))
     info = np.zeros(6)
-    _check(lib().pe_spectrum_aware_table(float(z), float(f), float(l), int(T), _dptr(tab), _dptr(info)))
+    _check(lib().pe_spectrum_aware_table_ex(float(z), float(f), float(l), int(T), float(z_safety),
+                                            PE_SPECTRUM_GATE if gate else 0, _dptr(tab), _dptr(info)))
     d = dict(zip(_SA_KEYS, info.tolist()))
     d["applied"] = bool(d["applied"])
     return tab, d
 
 
-def pe_polar_spectrum_aware(X, l: float, T: int, v0, dtype: str = "bf16", iters: int = 10, stream=None):
+def pe_polar_spectrum_aware(X, l: float, T: int, v0, dtype: str = "bf16", iters: int = 10, stream=None,
+                            z_safety: Optional[float] = None, gate: bool = False):
     """In place on a contiguous float32 CUDA matrix: the App. H cubic (when it
-    applies) and T Polar Express steps; returns the info dict."""
+    applies) and T Polar Express steps; returns the info dict. ``z_safety``
+    None is the library's default for its FP32 bound (1e-5)."""
     _fp32_matrix(X)
     v = _start_vector(X, v0)
     info = np.zeros(6)
-    _check(lib().pe_polar_spectrum_aware(ctypes.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], float(l), int(T),
-                                         DTYPES[dtype], v.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
-                                         int(iters), _dptr(info), ctypes.c_void_p(_stream_handle(stream))))
+    args = (ctypes.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], float(l), int(T), DTYPES[dtype],
+            v.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), int(iters))
+    if z_safety is None and not gate:
+        _check(lib().pe_polar_spectrum_aware(*args, _dptr(info), ctypes.c_void_p(_stream_handle(stream))))
+    else:
+        _check(lib().pe_polar_spectrum_aware_ex(*args, float(1e-5 if z_safety is None else z_safety),
+                                                PE_SPECTRUM_GATE if gate else 0, _dptr(info),
+                                                ctypes.c_void_p(_stream_handle(stream))))
     d = dict(zip(_SA_KEYS, info.tolist()))
     d["applied"] = bool(d["applied"])
     return d

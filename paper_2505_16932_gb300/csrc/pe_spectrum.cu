@@ -8,9 +8,13 @@
 //      singular value <= w = sqrt(f^2 - z^2); when the intervals are disjoint
 //      the odd cubic p(x) = a x + b x^3 with p(w) = p(z) = 1 (Eq. init_poly,
 //      written for f = 1; here that polynomial of x / f) maps the spectrum
-//      into [min(l / w, p(f)), 1], and Polar Express continues from there,
-//      if that composition's final greedy bound beats the plain one with one
-//      more step (the cubic pays off when z is close to f).
+//      into [min(l / w, p(f)), 1], and Polar Express continues from there;
+//      otherwise T + 1 ordinary steps. Two options that the appendix does not
+//      have: a relative shrink of z before use (pe_polar_spectrum_aware
+//      shrinks its FP32 bound by 1e-5 so that rounding cannot lift it above
+//      sigma_1), and a gate that keeps the cubic only when the composition
+//      after it reaches a better final greedy bound than the plain one with
+//      one more step.
 // The power method is memory-bound matrix-vector work on G itself (two
 // passes per iteration); its kernels are plain coalesced FP32 streams with
 // deterministic reductions (fixed summation order, FP64 norms).
@@ -29,7 +33,7 @@ namespace {
 constexpr int kRowWarps = 8;        // rows per block of the row-dot kernel (one warp each)
 constexpr int kColThreads = 256;    // columns-per-block / 4 (vector) of the column kernel
 constexpr int kColRows = 64;        // rows per block of the column kernel
-constexpr double kZSafety = 1e-5;   // relative shrink of z before use (FP32 rounding)
+constexpr double kZSafetyFp32 = 1e-5;   // relative shrink of an FP32 bound z before use
 
 // out[i] = sum_j M[i, j] x[j] for the m rows of M (m x n row-major); one warp per row
 __global__ void rowdot_kernel(const float* __restrict__ M, int64_t m, int64_t n, const float* __restrict__ x,
@@ -279,13 +283,16 @@ int pe_spectrum_bound(const void* X, int64_t m, int64_t n, const float* v0, int 
     return PE_OK;
 }
 
-int pe_spectrum_aware_table(double z, double f, double l, int T, double* table, double* info) {
+int pe_spectrum_aware_table_ex(double z, double f, double l, int T, double z_safety, unsigned flags, double* table,
+                               double* info) {
     using namespace pe;
     if (!table) return sfail(PE_EINVAL, "table is NULL");
     if (!(l > 0.0 && l <= 1.0)) return sfail(PE_EINVAL, "l must be in (0, 1]");
     if (T < 0 || T + 1 > kMaxSteps) return sfail(PE_EINVAL, "T must be in 0..63");
     if (!std::isfinite(z) || !std::isfinite(f) || z < 0.0 || f < 0.0) return sfail(PE_EINVAL, "bad z or f");
-    const double zs = z * (1.0 - kZSafety);
+    if (!(z_safety >= 0.0 && z_safety < 1.0)) return sfail(PE_EINVAL, "z_safety must be in [0, 1)");
+    if (flags & ~(unsigned)PE_SPECTRUM_GATE) return sfail(PE_EINVAL, "unknown flags");
+    const double zs = z * (1.0 - z_safety);
     double a = 0.0, b = 0.0, w = 0.0;
     const char* why = nullptr;
     // the plain composition with one more step, and its greedy bound after the last step
@@ -295,8 +302,7 @@ int pe_spectrum_aware_table(double z, double f, double l, int T, double* table, 
     bool applied = init_cubic(zs, f, &a, &b, &w);
     double lp = l;
     if (applied) {
-        // the cubic, then the composition for [l', 1]; kept only if its final
-        // greedy bound beats the plain one (the cubic pays off when z is near f)
+        // the cubic, then the composition for [l', 1]
         const double pf = f * (a + b * f * f);
         lp = std::min(l / w, pf);
         double l_final = lp;
@@ -306,7 +312,7 @@ int pe_spectrum_aware_table(double z, double f, double l, int T, double* table, 
             if (r != PE_OK) return sfail(r, why ? why : "coefficient solve failed");
             l_final = rbounds[2 * T];
         }
-        applied = l_final > pbounds[2 * (T + 1)];
+        if (flags & PE_SPECTRUM_GATE) applied = l_final > pbounds[2 * (T + 1)];
         if (applied) {
             table[0] = a;
             table[1] = b;
@@ -329,22 +335,33 @@ int pe_spectrum_aware_table(double z, double f, double l, int T, double* table, 
     return PE_OK;
 }
 
-int pe_polar_spectrum_aware(void* X, int64_t m, int64_t n, double l, int T, int dtype, const float* v0, int iters,
-                            double* info, void* stream) {
+int pe_spectrum_aware_table(double z, double f, double l, int T, double* table, double* info) {
+    return pe_spectrum_aware_table_ex(z, f, l, T, 0.0, 0u, table, info);
+}
+
+int pe_polar_spectrum_aware_ex(void* X, int64_t m, int64_t n, double l, int T, int dtype, const float* v0, int iters,
+                               double z_safety, unsigned flags, double* info, void* stream) {
     using namespace pe;
     if (dtype != PE_FP32 && dtype != PE_BF16 && dtype != PE_BF16X3) return sfail(PE_EINVAL, "bad dtype");
     if (T < 0 || T + 1 > kMaxSteps) return sfail(PE_EINVAL, "T must be in 0..63");
     if (!(l > 0.0 && l <= 1.0)) return sfail(PE_EINVAL, "l must be in (0, 1]");
+    if (!(z_safety >= 0.0 && z_safety < 1.0)) return sfail(PE_EINVAL, "z_safety must be in [0, 1)");
+    if (flags & ~(unsigned)PE_SPECTRUM_GATE) return sfail(PE_EINVAL, "unknown flags");
     double z = 0.0, f = 0.0;
     int r = pe_spectrum_bound(X, m, n, v0, iters, &z, &f, stream);
     if (r != PE_OK) return r;
     std::vector<double> table(3 * (T + 1));
     double inf[6];
-    r = pe_spectrum_aware_table(z, f, l, T, table.data(), inf);
+    r = pe_spectrum_aware_table_ex(z, f, l, T, z_safety, flags, table.data(), inf);
     if (r != PE_OK) return r;
     if (info)
         for (int k = 0; k < 6; ++k) info[k] = inf[k];
     return pe_polar(X, m, n, table.data(), T + 1, dtype, stream);
+}
+
+int pe_polar_spectrum_aware(void* X, int64_t m, int64_t n, double l, int T, int dtype, const float* v0, int iters,
+                            double* info, void* stream) {
+    return pe_polar_spectrum_aware_ex(X, m, n, l, T, dtype, v0, iters, pe::kZSafetyFp32, 0u, info, stream);
 }
 
 }  // extern "C"

@@ -158,17 +158,24 @@ def test_spectrum_entry_argument_errors_without_gpu(L):
     assert L.pe_spectrum_aware_table(0.9, 1.0, 1e-3, -1, tab.ctypes.data_as(P), None) == pe.PE_EINVAL
     assert L.pe_spectrum_aware_table(0.9, 1.0, 2.0, 5, tab.ctypes.data_as(P), None) == pe.PE_EINVAL
     assert L.pe_spectrum_aware_table(float("nan"), 1.0, 1e-3, 5, tab.ctypes.data_as(P), None) == pe.PE_EINVAL
+    assert L.pe_spectrum_aware_table_ex(0.9, 1.0, 1e-3, 5, 1.0, 0, tab.ctypes.data_as(P), None) == pe.PE_EINVAL
+    assert L.pe_spectrum_aware_table_ex(0.9, 1.0, 1e-3, 5, -1e-3, 0, tab.ctypes.data_as(P), None) == pe.PE_EINVAL
+    assert L.pe_spectrum_aware_table_ex(0.9, 1.0, 1e-3, 5, 0.0, 2, tab.ctypes.data_as(P), None) == pe.PE_EINVAL
+    assert L.pe_polar_spectrum_aware_ex(fake, 4, 8, 1e-3, 5, pe.PE_BF16, v.ctypes.data_as(F), 5, 0.0, 4,
+                                        info.ctypes.data_as(P), None) == pe.PE_EINVAL
 
 
+@pytest.mark.parametrize("z_safety,gate", [(0.0, False), (1e-5, False), (0.0, True), (1e-5, True)])
 @pytest.mark.parametrize("z,f,l,T", [(0.95, 0.99, 1e-3, 5), (0.999, 0.99999, 1e-7, 8), (0.72, 1.0, 1e-4, 3),
                                      (0.5, 0.99, 1e-3, 5), (0.7, 0.99, 1e-3, 4), (0.9, 1.0, 1e-3, 0),
-                                     (0.0, 0.0, 1e-3, 5)])
-def test_spectrum_aware_table_matches_oracle(L, z, f, l, T):
-    """Host table of the App. H initialisation against the oracle's: the cubic
-    row to rounding, the following composition from the same l'."""
+                                     (0.0, 0.0, 1e-3, 5), (0.8, 1.0, 1e-4, 4)])
+def test_spectrum_aware_table_matches_oracle(L, z, f, l, T, z_safety, gate):
+    """Host table of the App. H initialisation against the oracle's, with the
+    appendix's rule and with each option: the cubic row to rounding, the
+    following composition from the same l'."""
     from oracle import spectrum_init as S
-    tab, info = pe.pe_spectrum_aware_table(z, f, l, T)
-    ref, rinfo = S.spectrum_aware_table(z, f, l, T)
+    tab, info = pe.pe_spectrum_aware_table(z, f, l, T, z_safety=z_safety, gate=gate)
+    ref, rinfo = S.spectrum_aware_table(z, f, l, T, z_safety=z_safety, gate=gate)
     assert info["applied"] == rinfo["applied"]
     assert tab.shape == (T + 1, 3) and len(ref) == T + 1
     assert np.allclose(tab, np.array(ref), rtol=1e-12, atol=0)

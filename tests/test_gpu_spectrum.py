@@ -5,9 +5,11 @@
   lengths that are and are not multiples of 4, and at a full GPT-2 MLP size;
   z never exceeds sigma_1.
 * pe_polar_spectrum_aware (bound, host table, then the ordinary iteration)
-  against the oracle's spectrum_aware_polar: FP32 within 1e-5, BF16 and BF16x3
-  within 2e-2 relative Frobenius; without a dominant singular value it is bitwise
-  the plain call with T + 1 steps; the zero matrix stays zero.
+  against the oracle's spectrum_aware_polar with the appendix's rule: FP32
+  within 1e-5, BF16 and BF16x3 within 2e-2 relative Frobenius, l' within the
+  propagated bound error; the gate option both ways; without a dominant
+  singular value it is bitwise the plain call with T + 1 steps; the zero
+  matrix stays zero.
 * the appendix's power-law example (32 x 32, sigma_j = j^-5): with the cubic
   counted as an iteration, the FP32 GPU result is closer to U V^T than plain
   Polar Express at the same step count (by less than in FP64: the smallest
@@ -72,23 +74,56 @@ def test_bound_matches_oracle(m, n, iters):
 
 @pytest.mark.parametrize("m,n", [(200, 520), (520, 200), (255, 255)])
 def test_initialised_iteration_matches_oracle(m, n):
-    # sigma_2 / sigma_1 = 0.03 keeps the cubic; T = 6 from l = 5e-4 nearly
-    # converges, so the result does not amplify the FP32 bound's rounding (in
-    # the oracle a relative 1e-6 change of z moves it by 5e-9 here, by 5e-6
-    # at T = 5). sigma_min = 1e-3 keeps the FP32 iteration itself within
-    # 1e-5 (with sigma_min = 1e-4 FP32 rounding alone gives ~3e-5)
-    G, _, _, _ = _gapped(m + 3 * n, m, n, tail=(0.03, 1e-3))
+    """A gapped spectrum (sigma_2 / sigma_1 = 0.1, then log-spaced down to
+    1e-3; l = 1e-3), the appendix's rule, against the oracle with the same
+    z shrink the entry point applies to its FP32 bound (1e-5). l' = l / w
+    depends on z through w = sqrt(f^2 - z^2) only, so its relative
+    difference is the bound's relative difference times z^2 / w^2 (to first
+    order; 4.5 here); the bound itself is within 1e-5 of the FP64 power
+    method (test_bound_matches_oracle). T = 6 nearly converges, so the
+    output moves by 6e-3 of the bound's relative change (T = 5: by 2.9x) and
+    the FP32 bar is the iteration's own (3.5e-6 in a numpy FP32 run)."""
+    G, _, _, _ = _gapped(m + 3 * n, m, n)
     G32 = G.astype(np.float32).astype(np.float64)
     v0 = np.random.default_rng(2).standard_normal(min(m, n)).astype(np.float32)
-    ref, table, rinfo = S.spectrum_aware_polar(G32, 5e-4, 6, v0.astype(np.float64), 10)
+    ref, table, rinfo = S.spectrum_aware_polar(G32, 1e-3, 6, v0.astype(np.float64), 10, z_safety=1e-5)
     assert rinfo["applied"]
+    z, w = rinfo["z"], rinfo["w"]
     for dtype, tol in (("fp32", 1e-5), ("bf16", 2e-2), ("bf16x3", 2e-2)):
         X = dev(G)
-        info = pe.pe_polar_spectrum_aware(X, 5e-4, 6, v0, dtype, iters=10)
+        info = pe.pe_polar_spectrum_aware(X, 1e-3, 6, v0, dtype, iters=10)
         pe.pe_sync_status()
         assert info["applied"]
-        assert abs(info["l_after"] - rinfo["l_after"]) <= 1e-4 * rinfo["l_after"]
+        dz = (info["z"] - z) / z
+        assert abs(dz) <= 1e-5
+        dl = (info["l_after"] - rinfo["l_after"]) / rinfo["l_after"]
+        pred = dz * z * z / (w * w)
+        assert abs(dl - pred) <= 1e-3 * abs(pred) + 1e-9, (dl, pred)
         assert O.rel_fro(X.cpu().numpy().astype(np.float64), ref) <= tol, dtype
+
+
+def test_gate_option_matches_oracle():
+    """PE_SPECTRUM_GATE (not the appendix's rule): on a 1/i spectrum the
+    intervals are disjoint, the appendix applies the cubic, and the gate
+    keeps the plain composition; the entry point follows the oracle both ways
+    and the gated call is bitwise the plain call with T + 1 steps."""
+    rng = np.random.default_rng(8)
+    m, n = 256, 640
+    U, V = _haar(rng, m, m), _haar(rng, n, m)
+    s = 1.0 / np.arange(1, m + 1)
+    G = (U * s) @ V.T
+    v0 = rng.standard_normal(m).astype(np.float32)
+    for gate in (False, True):
+        _, _, rinfo = S.spectrum_aware_polar(G.astype(np.float32).astype(np.float64), 1e-3, 4,
+                                             v0.astype(np.float64), 10, z_safety=1e-5, gate=gate)
+        X = dev(G)
+        info = pe.pe_polar_spectrum_aware(X, 1e-3, 4, v0, "bf16", iters=10, gate=gate)
+        pe.pe_sync_status()
+        assert info["applied"] == rinfo["applied"] == (not gate)
+    Y = dev(G)
+    pe.pe_polar(Y, pe.pe_coeffs(5, 1e-3, 5, 1.01), "bf16")
+    pe.pe_sync_status()
+    assert torch.equal(X, Y)
 
 
 def test_no_dominant_value_is_the_plain_call():

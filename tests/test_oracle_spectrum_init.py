@@ -103,23 +103,47 @@ def test_cubic_step_is_the_scalar_map_on_singular_values():
     assert np.all(px >= np.minimum(x / w, pf) * (1 - 1e-12))
 
 
-def test_cubic_kept_only_when_its_final_bound_is_better():
-    """Spectra 1/i (the GPT-2-like workload): the intervals are disjoint but
-    the tail gains only f / w ~ 1.6, less than a quintic step, so the plain
-    composition is kept, and it is indeed the more accurate one; a gap of
-    100 (sigma_2 = 0.01) keeps the cubic, which is then the more accurate."""
+def _spectra(tail):
+    k = 768
+    s = 1.0 / np.arange(1, k + 1) if tail is None else np.concatenate([[1.0], np.geomspace(*tail, k - 1)])
+    x = s / (1.01 * np.linalg.norm(s) + 1e-7)
+    return x, float(np.linalg.norm(x)), float(x.max())
+
+
+def _forced(z, f, l, T):
+    a, b, w = S.init_cubic(z, f)
+    rest = O.optimal_composition(min(l / w, a * f + b * f ** 3), T, safety=1.01)[0]
+    return [(a, b, 0.0)] + [tuple(r) for r in rest]
+
+
+@pytest.mark.parametrize("tail", [None, (0.01, 1e-4)])
+def test_paper_rule_applies_the_cubic_whenever_the_intervals_are_disjoint(tail):
+    """The appendix builds the cubic whenever [0, w] and [z, f] are disjoint:
+    the table is the cubic followed by the composition for [l', 1], without
+    any further condition, whatever it does to the final error."""
+    x, f, z = _spectra(tail)
+    assert 2 * z * z > f * f
+    table, info = S.spectrum_aware_table(z, f, 1e-4, 4)
+    assert info["applied"] and info["z"] == z
+    assert np.array_equal(np.array(table), np.array(_forced(z, f, 1e-4, 4)))
+    # the z shrink option moves z, and only z
+    table2, info2 = S.spectrum_aware_table(z, f, 1e-4, 4, z_safety=1e-5)
+    assert info2["z"] == z * (1 - 1e-5)
+    assert np.array_equal(np.array(table2), np.array(_forced(z * (1 - 1e-5), f, 1e-4, 4)))
+
+
+def test_gate_keeps_the_cubic_only_when_its_final_bound_is_better():
+    """The gate option (not the appendix's rule). Spectra 1/i (the GPT-2-like
+    workload): the intervals are disjoint but the tail gains only f / w ~ 1.6,
+    less than a quintic step, so the gate keeps the plain composition, and it
+    is indeed the more accurate one; a gap of 100 (sigma_2 = 0.01) keeps the
+    cubic, which is then the more accurate."""
     for tail, keep in ((None, False), ((0.01, 1e-4), True)):
-        k = 768
-        s = 1.0 / np.arange(1, k + 1) if tail is None else np.concatenate([[1.0], np.geomspace(*tail, k - 1)])
-        x = s / (1.01 * np.linalg.norm(s) + 1e-7)
-        f, z = float(np.linalg.norm(x)), float(x.max())
-        assert 2 * z * z > f * f
-        table, info = S.spectrum_aware_table(z, f, 1e-4, 4)
+        x, f, z = _spectra(tail)
+        table, info = S.spectrum_aware_table(z, f, 1e-4, 4, gate=True)
         assert info["applied"] == keep
         plain, _ = O.optimal_composition(1e-4, 5, safety=1.01)
-        a, b, w = S.init_cubic(z * (1 - S.Z_SAFETY), f)
-        forced = [(a, b, 0.0)] + [tuple(r) for r in O.optimal_composition(min(1e-4 / w, a * f + b * f ** 3), 4,
-                                                                           safety=1.01)[0]]
+        forced = _forced(z, f, 1e-4, 4)
         e_plain = np.max(np.abs(O.compose_scalar(x, plain) - 1))
         e_forced = np.max(np.abs(O.compose_scalar(x, forced) - 1))
         assert (e_forced < e_plain) == keep, (e_forced, e_plain)
