@@ -391,6 +391,25 @@ def test_degree3_tables_skip_square(which):
                 assert O.rel_fro(X.cpu().numpy().astype(np.float64), ref) <= tol, (dtype, flags, G.shape)
 
 
+def test_jordan_table_through_same_kernels():
+    """Jordan's fixed quintic 3.4445x - 4.7750x^3 + 2.0315x^5 (Sec. 1.2) as a
+    table, through the same grouped kernels, against the FP64 iteration of
+    the same table. The polynomial does not contract (its singular values
+    keep oscillating in about [0.7, 1.2]), so rounding errors are not damped
+    and the BF16 error grows with T (a CPU emulation of the kernels'
+    arithmetic on this batch: 0.7e-2 - 1.6e-2 at T = 4, up to 2.6e-2 at
+    T = 6); T = 4 keeps every path within its stated bar."""
+    tab = np.array(O.jordan_table(4))
+    mats = _uneven(seed=5)
+    for dtype, tol in (("fp32", FP32_TOL), ("bf16", BF16_TOL), ("bf16x3", BF16_TOL)):
+        Xs = [to_dev(G) for G in mats]
+        pe.pe_polar_batched(Xs, tab, dtype)
+        pe.pe_sync_status()
+        for X, G in zip(Xs, mats):
+            ref = O.polar_express(G.astype(np.float32).astype(np.float64), tab)
+            assert O.rel_fro(X.cpu().numpy().astype(np.float64), ref) <= tol, (dtype, G.shape)
+
+
 # ------------------------------------------------------- host-buffer entry
 
 @pytest.mark.parametrize("ngroups", [0, 1, 2, 3])
