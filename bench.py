@@ -2,24 +2,33 @@
 """Benchmark of the Polar Express online stage on GB300.
 
 One "step" is one Muon orthogonalisation step of the workload: every matrix
-of the model normalised and taken through T polynomial steps by one
+of the set normalised and taken through T polynomial steps by one
 ``pe_polar_batched`` call (prepare launch + one persistent grouped tcgen05
 launch per polynomial step, replayed from a CUDA graph).
 
+The headline workload is the large dense set (8192 x 8192, 4096 x 14336,
+14336 x 4096; Haar singular vectors, singular values log-uniform in
+[1e-4, 1]; l = 1e-4, T = 6), generated on the GPU from a seeded generator.
 Reported ``value``: algorithmic polar TFLOP/s, sum over matrices of
 T (3 s^2 L + s^3) per step (s = min(m, n), L = max(m, n); the Gram and A^2
 products are symmetric and counted once), divided by the device time of the
-step, with inputs resident in HBM. ``e2e`` repeats the measurement with the
-inputs copied from pinned host memory and the factors copied back inside the
-timed region. ``roofline`` attributes device time to the dominant kernel
-from CUDA events bracketing each launch (library tracing) over the same
-steps. ``cpu_baseline`` times the FP64 oracle on the host cores on a bounded
-sample.
+step, with inputs resident in HBM. ``e2e`` repeats the measurement through
+the host-buffer entry ``pe_polar_batched_host`` with the inputs copied from
+pinned host memory and the factors copied back inside the timed region.
+``roofline`` attributes device time to the dominant kernel from CUDA events
+bracketing each launch (library tracing) over the same steps.
+``cpu_baseline`` times the FP64 oracle on the host cores on a bounded
+sample. ``fp32_plain`` and ``speedup_vs_fp32_plain`` compare with the plain
+FP32 path at equal restricted max|sigma - 1| (the smallest BF16 T whose
+error is no larger than the FP32 one at the workload's T). The GPT-2-small
+Muon step is reported beside it (``gpt2_small``) with its own roofline,
+e2e and CPU baseline.
 
 Launch: ``python bench.py [--gpus N] [--steps K] [--warmup W]``; for N > 1
-under torchrun, each rank runs its own copy of the workload (weak scaling)
-and rank 0 prints the line. ``--impl reference`` times the FP64 oracle on
-the host (the reference arm).
+under torchrun the matrices of one set are shared among the ranks (LPT on
+flops, one all-gather of the results inside the timed region; strong
+scaling) and rank 0 prints the line. ``--impl reference`` times the FP64
+oracle on the host (the reference arm).
 """
 from __future__ import annotations
 
@@ -32,7 +41,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -45,15 +53,17 @@ import synth  # noqa: E402
 
 METRIC = "polar TFLOP/s & µs/Muon-step, BF16 grouped vs FP32 plain at equal max|σ−1|"
 L2_BYTES = 129 * 1024 * 1024
+LARGE_SHAPES = ((8192, 8192), (4096, 14336), (14336, 4096))
+LARGE_NAME = "large_dense_8192sq_4096x14336_14336x4096"
 
-WORKLOADS = {
+CPU_WORKLOADS = {
     "gpt2_small": lambda: synth.gpt2_small(),
     "uneven_d1024": lambda: synth.uneven_d1024(),
     "gpt2_heads": lambda: synth.gpt2_heads(),
-    "large_dense": lambda: synth.large_dense(),
     "ill_conditioned": lambda: synth.ill_conditioned(),
     "plain_small": lambda: synth.plain_small(),
 }
+WORKLOADS = sorted(list(CPU_WORKLOADS) + ["large_dense"])
 
 
 def algorithmic_flops(shapes, T):
@@ -166,55 +176,101 @@ def cpu_cores():
     return os.cpu_count() or 1
 
 
-def accuracy_sample(wl):
-    """Indices of the accuracy sample: the first matrix of each distinct shape (up to 4)."""
-    seen = {}
-    for i, sh in enumerate(wl.shapes):
-        seen.setdefault(sh, i)
-    return list(seen.values())[:4]
-
-
-def cpu_baseline_leg(wl, table, budget_s: float, acc_idx):
-    """The leg of this script that runs the FP64 oracle: its timing on the
-    host cores (oracle_sample) and the FP64 iterates of the accuracy sample
-    (the spectral form where the factors are known, else the iteration on the
-    FP32-cast input), with the true polar factors. Returns (timing, refs)."""
+def oracle_sample(mats, table, budget_s: float):
+    """Time the FP64 oracle iteration over ``mats`` (host arrays) in order
+    until ``budget_s`` has elapsed (at least one matrix). A matrix whose full
+    iteration would overrun the budget (at an assumed 100 GFLOP/s FP64) is
+    sampled with its first polynomial step only. Returns (TFLOP/s, seconds,
+    matrices done, steps per matrix)."""
     import oracle as O
-    refs = {}
-    for i in acc_idx:
-        sv = wl.svd[i]
-        if sv is not None:
-            refs[i] = (O.polar_express_spectral(sv.U, sv.s, sv.V, table), sv.U @ sv.V.T)
-        else:
-            G = wl.matrices[i]
-            refs[i] = (O.polar_express(G.astype(np.float32).astype(np.float64), table), O.polar_svd(G))
-    return oracle_sample(wl, table, budget_s), refs
-
-
-def oracle_sample(wl, table, budget_s: float):
-    """Time the FP64 oracle iteration over the workload's matrices in order
-    until `budget_s` has elapsed (at least one matrix). Returns
-    (TFLOP/s, seconds, matrices done)."""
-    import oracle as O
-    done = 0
-    flops = 0.0
+    done, flops, steps_used = 0, 0.0, []
     t0 = time.perf_counter()
-    for G in wl.matrices:
-        # a matrix whose full iteration would overrun the budget (at an
-        # assumed 100 GFLOP/s FP64) is sampled with its first step only
+    for G in mats:
         steps = len(table)
         if dense_equiv_flops([G.shape], steps) / 1e11 > max(budget_s, 1.0):
             steps = 1
-        O.polar_express(G, table[:steps])
+        O.polar_express(np.asarray(G, dtype=np.float64), table[:steps])
         done += 1
+        steps_used.append(steps)
         flops += algorithmic_flops([G.shape], steps)
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
-    return flops / dt / 1e12, dt, done
+    return flops / dt / 1e12, dt, done, steps_used
 
 
-# ------------------------------------------------------------------ main
+def cpu_baseline_line(mats, table, budget_s, what):
+    tf, secs, done, steps = oracle_sample(mats, table, budget_s)
+    if all(s == len(table) for s in steps):
+        how = f"T={len(table)}"
+    else:
+        how = "the first polynomial step of each"
+    return {"value": tf, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"FP64 numpy oracle iteration of the first {done} of {len(mats)} matrices of {what}, "
+                      f"{how} ({secs:.1f} s)"}
+
+
+# ------------------------------------------------------------ workloads
+
+class Work:
+    """A workload resident on the GPU: FP32 inputs (never overwritten), known
+    factors where drawn that way (for restricted error metrics), host copies
+    on demand."""
+
+    def __init__(self, name, shapes, l, T, dev_in, facs=None, note="", svd=None, host=None):
+        self.name, self.shapes, self.l, self.T = name, [tuple(s) for s in shapes], l, T
+        self.dev_in, self.facs, self.note, self.svd = dev_in, facs, note, svd
+        self._host = host
+
+    def host(self):
+        if self._host is None:
+            self._host = [d.cpu().numpy() for d in self.dev_in]
+        return self._host
+
+
+def large_dense_gpu(torch, seed=3, shapes=LARGE_SHAPES):
+    """The large dense set on the GPU: G = U diag(s) V^T with U, V from the
+    QR of seeded Gaussian matrices (Haar) and s i.i.d. log-uniform in
+    [1e-4, 1], sorted; FP32. Keeps U1, V1: the singular directions with
+    s_i >= 1e-3 s_max (restricted metric)."""
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    mats, facs = [], []
+    for m, n in shapes:
+        k = min(m, n)
+        U, _ = torch.linalg.qr(torch.randn(m, k, device="cuda", generator=gen))
+        V, _ = torch.linalg.qr(torch.randn(n, k, device="cuda", generator=gen))
+        e = torch.rand(k, device="cuda", generator=gen) * 4.0 - 4.0
+        sv = torch.sort(10.0 ** e, descending=True).values
+        mats.append(((U * sv) @ V.T).contiguous())
+        keep = sv >= 1e-3 * sv[0]
+        facs.append((U[:, keep].contiguous(), V[:, keep].contiguous()))
+        del U, V
+    torch.cuda.empty_cache()
+    return Work(LARGE_NAME, shapes, 1e-4, 6, mats, facs,
+                "Haar U,V (QR of seeded Gaussians on the GPU); s log-uniform [1e-4,1]; l=1e-4, T=6")
+
+
+def load_workload(name, torch):
+    if name == "large_dense":
+        return large_dense_gpu(torch)
+    wl = CPU_WORKLOADS[name]()
+    host = [G.astype(np.float32) for G in wl.matrices]
+    dev = [torch.from_numpy(h).cuda() for h in host]
+    return Work(wl.name, wl.shapes, wl.l, wl.T, dev, None, wl.note, svd=wl.svd, host=host)
+
+
+def restricted_err(torch, xs, facs):
+    """max |sigma_i - 1| over the directions kept in facs: singular values
+    of U1^T X V1 (FP32 products, TF32 off)."""
+    worst = 0.0
+    for X, (U1, V1) in zip(xs, facs):
+        C = U1.T @ X @ V1
+        worst = max(worst, float((torch.linalg.svdvals(C) - 1.0).abs().max()))
+    return worst
+
+
+# ------------------------------------------------------------ reference arm
 
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -223,37 +279,53 @@ def dist_setup():
     return world, rank, local
 
 
-def run_reference(args, wl, world, rank):
+def run_reference(args, world, rank):
+    """The FP64 oracle on the host cores, the same metric and unit. Each step
+    is a bounded sample of the workload: the large dense set at a quarter of
+    its sides (2048^2, 1024 x 3584, 3584 x 1024, same spectrum law, l, T),
+    one matrix per step, cycling; other workloads: one of their matrices per
+    step."""
     if rank != 0:
         return 0
     import oracle as O
-    table, _ = O.optimal_composition(wl.l, wl.T, safety=1.01)
-    # each step: one matrix (cycling) through the FP64 iteration
-    n = len(wl.matrices)
+    if args.workload == "large_dense":
+        mats = []
+        for j, (m, n) in enumerate([(2048, 2048), (1024, 3584), (3584, 1024)]):
+            rng = np.random.default_rng(3 + j)
+            s = synth.spectrum_loguniform(rng, min(m, n), 1e-4, 1.0)
+            mats.append(synth.svd_matrix(rng, m, n, s).G)
+        name, l, T = LARGE_NAME, 1e-4, 6
+        sample = "FP64 numpy oracle iteration, T=6, of one quarter-side matrix of the large dense set per step"
+    else:
+        wl = CPU_WORKLOADS[args.workload]()
+        mats, name, l, T = wl.matrices, wl.name, wl.l, wl.T
+        sample = f"FP64 numpy oracle iteration, one matrix of {name} per step, T={T}"
+    table, _ = O.optimal_composition(l, T, safety=1.01)
+    n = len(mats)
     for i in range(args.warmup):
-        oracle_sample(synth.Workload(wl.name, [wl.matrices[i % n]], [None], wl.l, wl.T, wl.dtype), table, 0.0)
+        O.polar_express(mats[i % n], table[:1])
     tot_f, tot_t = 0.0, 0.0
     for i in range(args.steps):
-        G = wl.matrices[i % n]
+        G = mats[i % n]
         t0 = time.perf_counter()
         O.polar_express(G, table)
         tot_t += time.perf_counter() - t0
-        tot_f += algorithmic_flops([G.shape], wl.T)
+        tot_f += algorithmic_flops([G.shape], T)
     val = tot_f / tot_t / 1e12
-    cores = cpu_cores()
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "T": wl.T, "l": wl.l, "matrices": n,
-                   "step": "one matrix of the workload per step, cycling"},
-        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                         "sample": f"FP64 numpy oracle iteration, one matrix of {wl.name} per step, T={wl.T}"},
+        "config": {"workload": name, "T": T, "l": l, "matrices": n,
+                   "step": "one matrix of the sample per step, cycling"},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
 
+
+# ----------------------------------------------------------- roofline
 
 # source files whose contents decide each kernel's DRAM traffic
 KERNEL_SOURCES = {
@@ -285,14 +357,17 @@ def committed_traffic(workload: str, kernel: str):
     return None
 
 
-def roofline_line(trace, shapes, dtype, flops_step, in_bytes, workload, peaks):
+def roofline_line(trace, shapes, dtype, flops_step, in_bytes, workload, peaks, fp32_peak=None):
     """Roofline of the dominant kernel (largest traced time): algorithmic
     flops (or bytes) per launch over its mean CUDA-event launch time, against
     the measured burst peak (and the sustained one for tensor-bound kernels);
-    DRAM traffic from the committed ncu figure while the source matches."""
+    FP32 SIMT kernels against the measured cuBLAS FP32 (no TF32) rate when
+    given, else the derived SIMT roof; DRAM traffic from the committed ncu
+    figure while the source matches."""
     dom_name, (dom_n, dom_ms) = max(trace.items(), key=lambda kv: kv[1][1])
     dom_avg_ms = dom_ms / dom_n
     tot_trace_ms = sum(v[1] for v in trace.values())
+    peak_source = peaks["source"] + " burst"
     if dom_name in ("umma_step", "simt_update", "umma_update", "umma_gram", "umma_square", "simt_gram",
                     "simt_square"):
         if dom_name == "umma_step":
@@ -305,8 +380,13 @@ def roofline_line(trace, shapes, dtype, flops_step, in_bytes, workload, peaks):
                 f_launch += {"gram": s * s * L, "square": float(s) ** 3, "update": 2.0 * s * s * L}[key]
         achieved = f_launch / (dom_avg_ms * 1e-3) / 1e12
         if dtype == "fp32":
-            # FP32 SIMT roof: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock
-            peak, unit, bound = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12, "TFLOP/s", "alu"
+            if fp32_peak:
+                peak, unit, bound = fp32_peak, "TFLOP/s", "alu"
+                peak_source = "measured cuBLAS FP32 (TF32 off) 8192^3"
+            else:
+                # FP32 SIMT roof: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock
+                peak, unit, bound = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12, "TFLOP/s", "alu"
+                peak_source = "derived (152 SMs x 128 lanes x 2 x max SM clock)"
         else:
             peak, unit, bound = peaks["bf16_tflops"], "TFLOP/s", "tensor"
     else:
@@ -315,7 +395,7 @@ def roofline_line(trace, shapes, dtype, flops_step, in_bytes, workload, peaks):
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
                 "traffic": committed_traffic(workload, dom_name), "kernel": dom_name, "kernel_ms_avg": dom_avg_ms,
                 "launches_traced": dom_n, "share_of_step": dom_ms / tot_trace_ms,
-                "peak_source": peaks["source"] + " burst",
+                "peak_source": peak_source,
                 "algorithmic_bytes_per_launch_bf16": algorithmic_bytes_bf16(shapes, 1)}
     if bound == "tensor":
         roofline["peak_sustained"] = peaks["bf16_tflops_sustained"]
@@ -323,271 +403,161 @@ def roofline_line(trace, shapes, dtype, flops_step, in_bytes, workload, peaks):
     return roofline
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="gpt2_small", choices=sorted(WORKLOADS))
-    ap.add_argument("--dtype", default=None, choices=["fp32", "bf16", "bf16x3"])
-    ap.add_argument("--phased", action="store_true", help="three grouped launches per step")
-    ap.add_argument("--no-extras", action="store_true", help="skip the FP32 comparison and accuracy sample")
-    ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--no-largest", action="store_true", help="skip the largest-configuration measurement")
-    ap.add_argument("--sweep", action="store_true",
-                    help="error vs iteration count and vs time for FP32, BF16, BF16x3 and Newton-Schulz "
-                         "(ill-conditioned workload)")
-    args = ap.parse_args()
-    if args.steps < 1:
-        ap.error("--steps must be >= 1")
-    args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
+# ------------------------------------------------------------ measurement
 
-    world, rank, local = dist_setup()
-    wl = WORKLOADS[args.workload]()
-    if args.impl == "reference":
-        return run_reference(args, wl, world, rank)
+class Ctx:
+    def __init__(self, pe, torch, world, rank, local):
+        self.pe, self.torch = pe, torch
+        self.world, self.rank, self.local = world, rank, local
+        self.stream = torch.cuda.current_stream()
+        self.flush = torch.empty(max(2 * L2_BYTES, 256 << 20) // 4, dtype=torch.float32, device="cuda")
 
-    import torch
-    import paper_2505_16932_gb300 as pe
-    from paper_2505_16932_gb300 import build as B
-
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    B.build()
-    pe.lib()
-    dtype = args.dtype or ("bf16" if wl.dtype != "fp32" else "fp32")
-    table = pe.pe_coeffs(5, wl.l, wl.T, 1.01)
-    shapes = wl.shapes
-    T = wl.T
-    flops = algorithmic_flops(shapes, T)
-    flops_step = flops / T
-    host_in = [torch.from_numpy(G.astype(np.float32)).pin_memory() for G in wl.matrices]
-    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
-    dev_in = [h.to("cuda") for h in host_in]
-    dev_x = [d.clone() for d in dev_in]
-    in_bytes = sum(h.numel() * 4 for h in host_in)
-    flush = torch.empty(max(2 * L2_BYTES, 256 << 20) // 4, dtype=torch.float32, device="cuda")
-    flags = pe.PE_BATCH_PHASED if args.phased else 0
-    stream = torch.cuda.current_stream()
-
-    def restore():
-        for d, s in zip(dev_x, dev_in):
-            d.copy_(s, non_blocking=True)
-
-    def one_step(evs=None):
-        restore()
-        flush.fill_(1.0)
-        if evs:
-            evs[0].record(stream)
-        pe.pe_polar_batched(dev_x, table, dtype, flags=flags)
-        if evs:
-            evs[1].record(stream)
-
-    def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
+    def barrier(self):
+        self.torch.cuda.synchronize()
+        if self.world > 1:
             import torch.distributed as dist
             dist.barrier()
-        torch.cuda.synchronize()
+        self.torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if world == 1:
+    def max_over_ranks(self, x):
+        if self.world == 1:
             return x
         import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        t = self.torch.tensor([x], dtype=self.torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    for _ in range(args.warmup):
-        one_step()
-    pe.pe_sync_status()
 
-    # ---------------------------------------------------- timed region
-    sampler = ClockSampler(local)
-    if rank == 0:
+def time_calls(ctx, xs, src, table, dtype, n, flags=0):
+    """Mean CUDA-event time (ms) of ``n`` pe_polar_batched calls, each on
+    restored inputs after an L2 flush (restore and flush outside the events)."""
+    torch, pe = ctx.torch, ctx.pe
+    for _ in range(2):
+        for d, s in zip(xs, src):
+            d.copy_(s)
+        pe.pe_polar_batched(xs, table, dtype, flags=flags)
+    tot = 0.0
+    for _ in range(n):
+        for d, s in zip(xs, src):
+            d.copy_(s)
+        ctx.flush.fill_(3.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(ctx.stream)
+        pe.pe_polar_batched(xs, table, dtype, flags=flags)
+        b.record(ctx.stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / n
+
+
+def measure(ctx, wl, table, dtype, steps, warmup, flags=0, peaks=None, fp32_peak=None, clocks=True):
+    """The timed region (``steps`` grouped calls on resident inputs, each
+    restored and followed by an L2 flush outside the step's events), a traced
+    pass for the per-kernel roofline, and the end-to-end pass through the
+    host-buffer entry."""
+    torch, pe = ctx.torch, ctx.pe
+    T = len(table)
+    flops = algorithmic_flops(wl.shapes, T)
+    xs = [d.clone() for d in wl.dev_in]
+    in_bytes = sum(d.numel() * 4 for d in wl.dev_in)
+
+    def restore():
+        for d, s in zip(xs, wl.dev_in):
+            d.copy_(s, non_blocking=True)
+
+    for _ in range(warmup):
+        restore()
+        ctx.flush.fill_(1.0)
+        pe.pe_polar_batched(xs, table, dtype, flags=flags)
+    pe.pe_sync_status()
+    sampler = ClockSampler(ctx.local)
+    if clocks and ctx.rank == 0:
         sampler.start()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    ctx.barrier()
     l0 = pe.pe_launch_count()
     wall0 = time.perf_counter()
-    for k in range(args.steps):
-        one_step(evs[k])
-    barrier()
+    for k in range(steps):
+        restore()
+        ctx.flush.fill_(1.0)
+        evs[k][0].record(ctx.stream)
+        pe.pe_polar_batched(xs, table, dtype, flags=flags)
+        evs[k][1].record(ctx.stream)
+    ctx.barrier()
     wall = time.perf_counter() - wall0
     launches = pe.pe_launch_count() - l0
     pe.pe_sync_status()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    dev_ms = max_over_ranks(sum(step_ms))
-    ms_per_step = dev_ms / args.steps
-    value = world * flops * args.steps / (dev_ms * 1e-3) / 1e12
+    dev_ms = ctx.max_over_ranks(sum(step_ms))
+    ms_per_step = dev_ms / steps
+    value = flops * steps / (dev_ms * 1e-3) / 1e12
 
-    # ---------------------------------------------- per-kernel trace pass
+    # per-kernel trace pass (CUDA events around each launch on the call's stream)
     pe.pe_trace_enable(True)
-    for k in range(args.steps):
-        one_step()
+    for _ in range(steps):
+        restore()
+        ctx.flush.fill_(1.0)
+        pe.pe_polar_batched(xs, table, dtype, flags=flags)
     trace = pe.pe_trace_read()
     pe.pe_trace_enable(False)
     pe.pe_sync_status()
 
-    # -------------------------------------------------- end-to-end pass
-    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for _ in range(max(1, args.warmup)):   # builds and tunes the per-group plans outside the timed region
+    # end-to-end pass: pinned host inputs and outputs, copies inside the timed region
+    host_in = [torch.from_numpy(np.ascontiguousarray(h, dtype=np.float32)).pin_memory() for h in wl.host()]
+    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for _ in range(max(1, warmup)):   # builds and tunes the per-group plans outside the timed region
         pe.pe_polar_batched_host(host_in, host_out, table, dtype)
-    torch.cuda.synchronize()
-    barrier()
-    for k in range(args.steps):
-        flush.fill_(1.0)
-        e2e_ev[k][0].record(stream)
-        # the C ABI's host-buffer entry: copies in, grouped compute, copies
-        # out, pipelined by the library across groups of matrices
+    ctx.barrier()
+    for k in range(steps):
+        ctx.flush.fill_(1.0)
+        e2e_ev[k][0].record(ctx.stream)
         pe.pe_polar_batched_host(host_in, host_out, table, dtype)
-        e2e_ev[k][1].record(stream)
-    barrier()
-    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev))
-    e2e_value = world * flops * args.steps / (e2e_ms * 1e-3) / 1e12
-    clocks = sampler.stop() if rank == 0 else None
+        e2e_ev[k][1].record(ctx.stream)
+    ctx.barrier()
+    e2e_ms = ctx.max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev))
+    clk = sampler.stop() if (clocks and ctx.rank == 0) else None
     pe.pe_sync_status()
-
-    # ---------------------------------------------------------- roofline
-    roofline = roofline_line(trace, shapes, dtype, flops_step, in_bytes, wl.name, measured_peaks())
-
-    # ------------------------------------------ extras (rank 0, N = 1 style)
-    extras = {}
-    cpu = None
-    if rank == 0:
-        acc_idx = [] if args.no_extras else accuracy_sample(wl)
-        (tf, secs, done), refs = cpu_baseline_leg(wl, table, args.cpu_budget, acc_idx)
-        if not args.no_extras:
-            extras = accuracy_and_fp32(pe, torch, wl, table, dev_in, dtype, flush, stream, args, refs)
-            extras["newton_schulz5"] = newton_schulz_line(pe, torch, wl, dev_in, dtype, flush, stream, refs, args)
-            if dtype == "bf16":
-                extras["torch_cublas_bf16"] = cublas_listing_line(torch, wl, table, dev_in, flush, stream, refs,
-                                                                  ms_per_step, args)
-            extras["spectrum_bound"] = spectrum_bound_line(pe, wl, dev_in)
-        if args.sweep or wl.name == "ill_conditioned":
-            extras["error_vs_T"] = error_sweep(pe, torch, wl, dev_in, flush, stream)
-        if not args.no_largest and wl.name != "large_dense" and world == 1:
-            extras["largest_config"] = largest_config(pe, torch, flush, stream, min(args.steps, 10))
-        cpu = {"value": tf, "unit": "TFLOP/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"FP64 numpy oracle iteration of the first {done} of {len(shapes)} matrices, "
-                         f"T={T} ({secs:.1f} s)"}
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    if rank != 0:
-        return 0
-    line = {
-        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16" if dtype == "bf16" else dtype, "data": "synthetic",
-        "config": {"workload": wl.name, "matrices": len(shapes), "T": T, "l": wl.l, "path": dtype +
-                   (" grouped phased" if args.phased else " grouped persistent (one launch per step), CUDA graph"),
-                   "flops_per_step": flops, "dense_equiv_flops_per_step": dense_equiv_flops(shapes, T),
-                   "input_bytes": in_bytes, "l2": "inputs larger than L2 and a 258 MB L2 flush before each step",
-                   "note": wl.note},
-        "us_per_muon_step": 1e3 * ms_per_step,
-        "us_per_muon_step_median": 1e3 * statistics.median(step_ms),
-        "us_per_poly_step": 1e3 * ms_per_step / T,
-        "wall_s_timed": wall,
-        "gpu_launches": int(launches),
-        "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": in_bytes,
-                "ms_per_step": e2e_ms / args.steps},
-        "roofline": roofline,
-        "trace": {k: {"launches": v[0], "ms_total": v[1]} for k, v in trace.items()},
-        "clocks": clocks,
-        "cpu_baseline": cpu,
+    del host_in, host_out
+    roof = roofline_line(trace, wl.shapes, dtype, flops / T, in_bytes, wl.name, peaks or measured_peaks(),
+                         fp32_peak)
+    return {
+        "value": value, "ms_per_step": ms_per_step, "us_per_muon_step_median": 1e3 * statistics.median(step_ms),
+        "us_per_poly_step": 1e3 * ms_per_step / T, "wall_s_timed": wall, "gpu_launches": int(launches),
+        "flops_per_step": flops, "in_bytes": in_bytes, "xs": xs,
+        "e2e": {"value": flops * steps / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": in_bytes,
+                "d2h_bytes_per_step": in_bytes, "ms_per_step": e2e_ms / steps},
+        "roofline": roof, "trace": {k: {"launches": v[0], "ms_total": v[1]} for k, v in trace.items()},
+        "clocks": clk,
     }
-    worst = extras.pop("_worst", None)
-    line.update(extras)
-    if worst is not None:
-        w16, w32, ms32 = worst
-        # equal max|sigma - 1| at the same T: both paths apply the same table,
-        # so the BF16 error must not exceed the FP32 one by more than 5%
-        line["speedup_vs_fp32_plain"] = {
-            "value": ms32 / ms_per_step, "T_bf16": T, "T_fp32": T, "max_sigma_err_bf16": w16,
-            "max_sigma_err_fp32": w32, "equal_error": bool(w16 <= 1.05 * w32 + 1e-4)}
-    print(json.dumps(line))
-    return 0
 
 
-def largest_config(pe, torch, flush, stream, steps):
-    """The largest configuration (8192 x 8192, 4096 x 14336, 14336 x 4096;
-    Haar U, V; s log-uniform in [1e-4, 1]; l = 1e-4, T = 6), generated on the
-    GPU with a seeded torch generator (input plumbing only). Times the BF16
-    grouped path and the FP32 plain path and compares their max|sigma - 1|
-    restricted to sigma_i(G) >= 1e-3 sigma_max (computed on the GPU from the
-    known factors: singular values of U1^T X V1)."""
-    shapes = [(8192, 8192), (4096, 14336), (14336, 4096)]
-    T, l = 6, 1e-4
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(3)
-    mats, facs = [], []
-    for m, n in shapes:
-        k = min(m, n)
-        U, _ = torch.linalg.qr(torch.randn(m, k, device="cuda", generator=gen))
-        V, _ = torch.linalg.qr(torch.randn(n, k, device="cuda", generator=gen))
-        e = torch.rand(k, device="cuda", generator=gen) * 4.0 - 4.0
-        sv = torch.sort(10.0 ** e, descending=True).values
-        mats.append(((U * sv) @ V.T).contiguous())
-        keep = sv >= 1e-3 * sv[0]
-        facs.append((U[:, keep].contiguous(), V[:, keep].contiguous()))
-    table = pe.pe_coeffs(5, l, T, 1.01)
-    flops = algorithmic_flops(shapes, T)
-    out = {"workload": "large_dense_8192sq_4096x14336_14336x4096", "T": T, "l": l, "flops_per_step": flops}
-    xs = [x.clone() for x in mats]
-
-    def timed(path, tab, n):
-        for _ in range(2):
-            for d, s0 in zip(xs, mats):
-                d.copy_(s0)
-            pe.pe_polar_batched(xs, tab, path)
-        tot = 0.0
-        for _ in range(n):
-            for d, s0 in zip(xs, mats):
-                d.copy_(s0)
-            flush.fill_(3.0)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            pe.pe_polar_batched(xs, tab, path)
-            b.record(stream)
-            b.synchronize()
-            tot += a.elapsed_time(b)
-        return tot / n
-
-    def restricted_err():
-        worst = 0.0
-        for X, (U1, V1) in zip(xs, facs):
-            C = U1.T @ X @ V1                  # FP32 (TF32 off)
-            sv = torch.linalg.svdvals(C)
-            worst = max(worst, float((sv - 1.0).abs().max()))
-        return worst
-
-    ms16 = timed("bf16", table, max(3, steps))
-    e16 = restricted_err()
-    ms32 = timed("fp32", table, 2)
-    e32 = restricted_err()
-    # smallest BF16 step count whose restricted error matches the FP32 one
-    t16, ms16_eq, e16_eq = T, ms16, e16
-    while e16_eq > 1.05 * e32 + 1e-4 and t16 < T + 4:
-        t16 += 1
-        tab16 = pe.pe_coeffs(5, l, t16, 1.01)
-        ms16_eq = timed("bf16", tab16, 3)
-        e16_eq = restricted_err()
-    peaks = measured_peaks()
-    out["bf16"] = {"value": flops / (ms16 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms16,
-                   "frac_of_bf16_peak": flops / (ms16 * 1e-3) / 1e12 / peaks["bf16_tflops"],
-                   # the call runs for seconds under the power cap: the sustained figure applies too
-                   "frac_of_bf16_sustained": flops / (ms16 * 1e-3) / 1e12 / peaks["bf16_tflops_sustained"],
-                   "restricted_max_sigma_err": e16}
-    out["fp32_plain"] = {"value": flops / (ms32 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms32,
-                         "restricted_max_sigma_err": e32}
-    out["speedup_vs_fp32_plain_equal_err"] = {"value": ms32 / ms16_eq, "T_bf16": t16, "T_fp32": T,
-                                              "restricted_max_sigma_err_bf16": e16_eq,
-                                              "restricted_max_sigma_err_fp32": e32}
-    del xs, mats, facs
+def matmul_peaks(torch, n=8192, reps=6):
+    """cuBLAS rates on this GPU at n^3: FP32 with TF32 off (the SIMT rate the
+    plain FP32 path is measured against), FP32 with TF32 on, BF16."""
+    out = {}
+    old = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, dt, tf32 in (("fp32_simt", torch.float32, False), ("tf32", torch.float32, True),
+                               ("bf16", torch.bfloat16, False)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, device="cuda").to(dt)
+            b = torch.randn(n, n, device="cuda").to(dt)
+            for _ in range(2):
+                torch.matmul(a, b)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                torch.matmul(a, b)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            out[name + "_tflops"] = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    out["n"] = n
     torch.cuda.empty_cache()
     return out
 
@@ -595,157 +565,89 @@ def largest_config(pe, torch, flush, stream, steps):
 NS5_ROW = (15.0 / 8.0, -10.0 / 8.0, 3.0 / 8.0)   # the fixed Newton-Schulz quintic (Sec. 2)
 
 
-def newton_schulz_line(pe, torch, wl, dev_in, dtype, flush, stream, refs, args):
-    """The fixed-coefficient Newton-Schulz quintic, T = the workload's T, run
-    through the same kernels (same grouped call and graph): time per step and
-    max|sigma - 1| on the accuracy sample."""
-    table = np.array([NS5_ROW] * wl.T)
-    xs = [d.clone() for d in dev_in]
-    for _ in range(2):
-        for d, s in zip(xs, dev_in):
-            d.copy_(s)
-        pe.pe_polar_batched(xs, table, dtype)
-    n = max(3, min(20, args.steps // 5))
-    tot = 0.0
-    for _ in range(n):
-        for d, s in zip(xs, dev_in):
-            d.copy_(s)
-        flush.fill_(3.0)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        pe.pe_polar_batched(xs, table, dtype)
-        b.record(stream)
-        b.synchronize()
-        tot += a.elapsed_time(b)
-    ms = tot / n
-    errs = [_max_sigma_err(xs[i].cpu().numpy().astype(np.float64)) for i in sorted(refs)]
-    pe_errs = [_max_sigma_err(refs[i][0]) for i in sorted(refs)]
-    return {"value": algorithmic_flops(wl.shapes, wl.T) / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
-            "T": wl.T, "dtype": dtype, "max_sigma_err_sample": max(errs) if errs else None,
-            "polar_express_fp64_max_sigma_err_sample": max(pe_errs) if pe_errs else None}
-
-
-def cublas_listing_line(torch, wl, table, dev_in, flush, stream, refs, ours_ms, args):
-    """The same method written with PyTorch library calls (cuBLAS GEMMs), the
-    form of the paper's own online code (App. A): X, A and B stored in BF16,
-    one batched GEMM call per product for each stack of same-shape matrices,
-    the combinations b A + c A A and a X + B X folded into the GEMM calls
-    (baddbmm's beta and alpha), the whole step sequence replayed from a CUDA
-    graph. A comparison point for the kernels of this library, which it
-    does not call; time per Muon step and relative error on the accuracy
-    sample against the FP64 iteration."""
+def listing_steps(torch, wl, table):
+    """The paper's online code (App. A) in PyTorch: X, A and B stored in BF16,
+    one batched product call per product for each stack of same-shape
+    matrices, the combinations b A + c A A and a X + B X folded into the
+    product calls (baddbmm's beta and alpha). Returns (run, outputs)."""
     groups = {}
     for i, sh in enumerate(wl.shapes):
         groups.setdefault(sh, []).append(i)
-    stacks = [(sh, idx, torch.stack([dev_in[i] for i in idx])) for sh, idx in groups.items()]
+    stacks = [(sh, idx, torch.stack([wl.dev_in[i] for i in idx])) for sh, idx in groups.items()]
     outs = [torch.empty_like(G) for _, _, G in stacks]
     coef = [tuple(float(v) for v in row) for row in table]
 
-    def step_sequence():
-        for (sh, _, G), out in zip(stacks, outs):
-            nrm = torch.linalg.vector_norm(G, dim=(1, 2), keepdim=True)
-            X = (G / (1.01 * nrm + 1e-7)).to(torch.bfloat16)
-            if sh[0] > sh[1]:
-                X = X.mT                               # short side first
-            for a, b, c in coef:
-                A = torch.bmm(X, X.mT)
-                B = torch.baddbmm(A, A, A, beta=b, alpha=c)
-                X = torch.baddbmm(X, B, X, beta=a, alpha=1.0)
-            out.copy_(X.mT if sh[0] > sh[1] else X)
+    def one(G, tall):
+        nrm = torch.linalg.vector_norm(G, dim=(1, 2), keepdim=True)
+        X = (G / (1.01 * nrm + 1e-7)).to(torch.bfloat16)
+        if tall:
+            X = X.mT
+        for a, b, c in coef:
+            A = torch.bmm(X, X.mT)
+            B = torch.baddbmm(A, A, A, beta=b, alpha=c)
+            X = torch.baddbmm(X, B, X, beta=a, alpha=1.0)
+        return X.mT if tall else X
 
-    side = torch.cuda.Stream()
-    side.wait_stream(stream)
-    with torch.cuda.stream(side):
-        for _ in range(3):
-            step_sequence()
-    stream.wait_stream(side)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        step_sequence()
-    graph.replay()
-    n = max(3, min(20, args.steps // 5))
-    tot = 0.0
-    for _ in range(n):
-        flush.fill_(3.0)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        graph.replay()
-        b.record(stream)
-        b.synchronize()
-        tot += a.elapsed_time(b)
-    ms = tot / n
-    errs = []
-    for (sh, idx, _), out in zip(stacks, outs):
-        for k, i in enumerate(idx):
-            if i in refs:
-                errs.append(_rel_fro(out[k].cpu().numpy().astype(np.float64), refs[i][0]))
-    del graph, stacks, outs
-    torch.cuda.empty_cache()
-    return {"value": algorithmic_flops(wl.shapes, wl.T) / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
-            "T": wl.T, "kind": "torch bmm/baddbmm (cuBLAS) in BF16 per same-shape stack, CUDA graph",
-            "rel_fro_vs_fp64_iteration_sample_max": max(errs) if errs else None,
-            "speedup_of_this_library": ms / ours_ms}
+    return stacks, outs, one
 
 
-def spectrum_bound_line(pe, wl, dev_in, iters=10):
-    """Cost of the App. H bound (the power method, ``iters`` steps, on G) for
-    one matrix of each distinct shape: host wall time of the blocking call
-    (its buffers, about five launches per step and the read-back of z), and
-    z / f, which decides whether the cubic applies (z / f > 1 / sqrt 2)."""
-    seen = {}
-    for i, sh in enumerate(wl.shapes):
-        seen.setdefault(sh, i)
-    rows = []
-    for sh, i in list(seen.items())[:4]:
-        v0 = np.random.default_rng(i).standard_normal(min(sh)).astype(np.float32)
-        pe.pe_spectrum_bound(dev_in[i], v0, iters)
-        t0 = time.perf_counter()
-        z, f = pe.pe_spectrum_bound(dev_in[i], v0, iters)
-        rows.append({"shape": list(sh), "ms": 1e3 * (time.perf_counter() - t0), "z_over_f": z / f if f else None})
-    return {"iters": iters, "rows": rows}
+def listing_line(ctx, wl, table, ours_ms, compiled, n=5):
+    """The App. A listing on the same inputs, either eager cuBLAS calls
+    replayed from a CUDA graph or under torch.compile; time per Muon step."""
+    torch = ctx.torch
+    stacks, outs, one = listing_steps(torch, wl, table)
+    kind = "torch bmm/baddbmm (cuBLAS) in BF16 per same-shape stack, CUDA graph"
+    try:
+        if compiled:
+            fn = torch.compile(one, dynamic=False)
+            kind = "the App. A listing under torch.compile (default mode), BF16 per same-shape stack"
 
-
-def error_sweep(pe, torch, wl, dev_in, flush, stream, Ts=(2, 4, 6, 8, 10, 12), gamma=1e-3):
-    """Error against the truth U V^T vs iteration count T and vs time, for the
-    Polar Express tables (FP32 plain, BF16, BF16x3) and the Newton-Schulz
-    quintic (BF16), on a workload with known factors. Errors per T: the
-    largest over the workload's matrices of max|sigma_i - 1| restricted to the
-    directions with s_i >= gamma s_max (singular values of U1^T X V1, FP64 on
-    the GPU) and of ||X - U V^T||_F / sqrt(n)."""
-    kept = []
-    for sv in wl.svd:
-        k = sv.s >= gamma * sv.s.max()
-        U = torch.from_numpy(sv.U).cuda()
-        V = torch.from_numpy(sv.V).cuda()
-        kept.append((U[:, k].contiguous(), V[:, k].contiguous(), U, V))
-    rows = []
-    for T in Ts:
-        for path in ("fp32", "bf16", "bf16x3", "ns5"):
-            table = np.array([NS5_ROW] * T) if path == "ns5" else pe.pe_coeffs(5, wl.l, T, 1.01)
-            dt = "bf16" if path == "ns5" else path
-            xs = [d.clone() for d in dev_in]
-            pe.pe_polar_batched(xs, table, dt)            # plan, tuning
-            ms = 0.0
+            def run():
+                for (sh, _, G), out in zip(stacks, outs):
+                    out.copy_(fn(G, sh[0] > sh[1]))
             for _ in range(3):
-                for d, s in zip(xs, dev_in):
-                    d.copy_(s)
-                flush.fill_(4.0)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                pe.pe_polar_batched(xs, table, dt)
-                b.record(stream)
-                b.synchronize()
-                ms += a.elapsed_time(b) / 3
-            rmax, efro = 0.0, 0.0
-            for X, (U1, V1, U, V) in zip(xs, kept):
-                Xd = X.double()
-                sig = torch.linalg.svdvals(U1.T @ Xd @ V1)
-                rmax = max(rmax, float((sig - 1).abs().max()))
-                efro = max(efro, float(torch.linalg.norm(Xd - U @ V.T) / np.sqrt(min(X.shape))))
-            rows.append({"path": path, "T": T, "ms": ms, "restricted_max_sigma_err": rmax,
-                         "err_fro_per_sqrt_n": efro})
-            del xs
-    return {"gamma": gamma, "rows": rows}
+                run()
+            torch.cuda.synchronize()
+            replay = run
+        else:
+            def run():
+                for (sh, _, G), out in zip(stacks, outs):
+                    out.copy_(one(G, sh[0] > sh[1]))
+            side = torch.cuda.Stream()
+            side.wait_stream(ctx.stream)
+            with torch.cuda.stream(side):
+                for _ in range(3):
+                    run()
+            ctx.stream.wait_stream(side)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                run()
+            replay = graph.replay
+        replay()
+        tot = 0.0
+        for _ in range(n):
+            ctx.flush.fill_(3.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(ctx.stream)
+            replay()
+            b.record(ctx.stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        ms = tot / n
+    except Exception as e:   # noqa: BLE001 - a comparison point only
+        return {"unavailable": f"{type(e).__name__}: {str(e).splitlines()[0][:200] if str(e) else ''}", "kind": kind}
+    res = {"value": algorithmic_flops(wl.shapes, len(table)) / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+           "ms_per_step": ms, "T": len(table), "kind": kind, "speedup_of_this_library": ms / ours_ms}
+    if wl.facs is not None:
+        xs = []
+        for (sh, idx, _), out in zip(stacks, outs):
+            for k in range(len(idx)):
+                xs.append((idx[k], out[k]))
+        xs.sort(key=lambda t: t[0])
+        res["restricted_max_sigma_err"] = restricted_err(torch, [x for _, x in xs], wl.facs)
+    del stacks, outs
+    torch.cuda.empty_cache()
+    return res
 
 
 def _rel_fro(X, Y):
@@ -760,52 +662,348 @@ def _max_sigma_err(X):
     return float(np.max(np.abs(np.linalg.svd(X, compute_uv=False) - 1.0)))
 
 
-def accuracy_and_fp32(pe, torch, wl, table, dev_in, dtype, flush, stream, args, refs):
-    """FP32 plain path on the same workload (time per step) and errors of the
-    accuracy sample against the FP64 iterates ``refs`` that the cpu_baseline
-    leg computed."""
+def accuracy_sample(wl, table, xs, k=4):
+    """First matrix of each distinct shape (up to k): relative Frobenius
+    distance to the FP64 iterate (the oracle's spectral form where the factors
+    are known, else its iteration on the FP32-cast input), error against the
+    true factor and max|sigma - 1|."""
+    import oracle as O
+    seen = {}
+    for i, sh in enumerate(wl.shapes):
+        seen.setdefault(sh, i)
+    rows = []
+    for i in list(seen.values())[:k]:
+        got = xs[i].cpu().numpy().astype(np.float64)
+        sv = wl.svd[i] if wl.svd else None
+        if sv is not None:
+            ref, P = O.polar_express_spectral(sv.U, sv.s, sv.V, table), sv.U @ sv.V.T
+        else:
+            G = wl.host()[i].astype(np.float64)
+            ref, P = O.polar_express(G, table), O.polar_svd(G)
+        rows.append({"shape": list(wl.shapes[i]), "rel_fro_vs_fp64_iteration": _rel_fro(got, ref),
+                     "err_fro_per_sqrt_n": _err_fro(got, P), "max_sigma_err": _max_sigma_err(got),
+                     "fp64_max_sigma_err": _max_sigma_err(ref)})
+    return rows
+
+
+def large_extras(ctx, wl, table, res, dtype, peaks, mm, args):
+    """Large dense set: restricted max|sigma - 1| of the BF16 result, the plain
+    FP32 path at the same T, and the smallest BF16 T whose restricted error is
+    no larger than FP32's (speed-up at equal error)."""
+    torch, pe = ctx.torch, ctx.pe
     out = {}
-    xs = [d.clone() for d in dev_in]
-    # FP32 plain timing
-    for _ in range(2):
-        for d, s in zip(xs, dev_in):
-            d.copy_(s)
-        pe.pe_polar_batched(xs, table, "fp32")
-    n = max(3, min(20, args.steps // 5))
-    tot = 0.0
-    for _ in range(n):
-        for d, s in zip(xs, dev_in):
-            d.copy_(s)
-        flush.fill_(2.0)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        pe.pe_polar_batched(xs, table, "fp32")
-        b.record(stream)
-        b.synchronize()
-        tot += a.elapsed_time(b)
-    ms32 = tot / n
-    flops = algorithmic_flops(wl.shapes, wl.T)
-    idx = sorted(refs)
-    res = {}
-    for path in (dtype, "fp32"):
-        xs2 = [dev_in[i].clone() for i in idx]
-        pe.pe_polar_batched(xs2, table, path)
-        torch.cuda.synchronize()
-        errs = []
-        for j, i in enumerate(idx):
-            got = xs2[j].cpu().numpy().astype(np.float64)
-            ref, P = refs[i]
-            errs.append({"shape": list(wl.shapes[i]), "rel_fro_vs_fp64_iteration": _rel_fro(got, ref),
-                         "err_fro_per_sqrt_n": _err_fro(got, P), "max_sigma_err": _max_sigma_err(got),
-                         "fp64_max_sigma_err": _max_sigma_err(ref)})
-        res[path] = errs
-    worst16 = max(e["max_sigma_err"] for e in res[dtype])
-    worst32 = max(e["max_sigma_err"] for e in res["fp32"])
-    out["fp32_plain"] = {"value": flops / (ms32 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms32,
-                         "max_sigma_err_sample": worst32, "T": wl.T}
-    out["accuracy"] = res
-    out["_worst"] = (worst16, worst32, ms32)
+    e16 = restricted_err(torch, res["xs"], wl.facs)
+    xs = [d.clone() for d in wl.dev_in]
+    ms32 = time_calls(ctx, xs, wl.dev_in, table, "fp32", 2)
+    e32 = restricted_err(torch, xs, wl.facs)
+    t16, ms16, err16 = wl.T, res["ms_per_step"], e16
+    tries = []
+    while err16 > 1.05 * e32 + 1e-4 and t16 < wl.T + 4:
+        t16 += 1
+        tab16 = pe.pe_coeffs(5, wl.l, t16, 1.01)
+        ms16 = time_calls(ctx, xs, wl.dev_in, tab16, dtype, 3)
+        err16 = restricted_err(torch, xs, wl.facs)
+        tries.append({"T": t16, "ms": ms16, "restricted_max_sigma_err": err16})
+    f = algorithmic_flops(wl.shapes, wl.T)
+    fp32 = {"value": f / (ms32 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms32, "T": wl.T,
+            "restricted_max_sigma_err": e32}
+    if mm and mm.get("fp32_simt_tflops"):
+        fp32["frac_of_measured_fp32_simt"] = fp32["value"] / mm["fp32_simt_tflops"]
+    out["fp32_plain"] = fp32
+    out["accuracy"] = {"restricted_max_sigma_err_bf16": e16, "restricted_max_sigma_err_fp32": e32,
+                       "gamma": 1e-3, "note": "max|sigma_i - 1| over the directions with s_i >= 1e-3 s_max "
+                                               "(singular values of U1^T X V1)"}
+    out["speedup_vs_fp32_plain"] = {"value": ms32 / ms16, "T_bf16": t16, "T_fp32": wl.T,
+                                    "restricted_max_sigma_err_bf16": err16,
+                                    "restricted_max_sigma_err_fp32": e32, "equal_error": bool(err16 <= 1.05 * e32 + 1e-4),
+                                    "search": tries}
+    tab_ns = np.array([NS5_ROW] * wl.T)
+    ms_ns = time_calls(ctx, xs, wl.dev_in, tab_ns, dtype, 3)
+    out["newton_schulz5"] = {"value": f / (ms_ns * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms_ns, "T": wl.T,
+                             "dtype": dtype, "restricted_max_sigma_err": restricted_err(torch, xs, wl.facs)}
+    del xs
+    torch.cuda.empty_cache()
     return out
+
+
+def small_extras(ctx, wl, table, res, dtype, args):
+    """Workloads generated on the CPU: accuracy sample against the FP64
+    oracle, the FP32 path, the Newton-Schulz quintic through the same
+    kernels."""
+    torch, pe = ctx.torch, ctx.pe
+    out = {"accuracy": {dtype: accuracy_sample(wl, table, res["xs"])}}
+    xs = [d.clone() for d in wl.dev_in]
+    n = max(3, min(20, args.steps // 5))
+    ms32 = time_calls(ctx, xs, wl.dev_in, table, "fp32", n)
+    out["accuracy"]["fp32"] = accuracy_sample(wl, table, xs)
+    f = algorithmic_flops(wl.shapes, wl.T)
+    w16 = max(r["max_sigma_err"] for r in out["accuracy"][dtype])
+    w32 = max(r["max_sigma_err"] for r in out["accuracy"]["fp32"])
+    out["fp32_plain"] = {"value": f / (ms32 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms32, "T": wl.T,
+                         "max_sigma_err_sample": w32}
+    # both paths apply the same table, so at equal T the BF16 error must
+    # not exceed the FP32 one by more than 5%
+    out["speedup_vs_fp32_plain"] = {"value": ms32 / res["ms_per_step"], "T_bf16": wl.T, "T_fp32": wl.T,
+                                    "max_sigma_err_bf16": w16, "max_sigma_err_fp32": w32,
+                                    "equal_error": bool(w16 <= 1.05 * w32 + 1e-4)}
+    tab_ns = np.array([NS5_ROW] * wl.T)
+    ms_ns = time_calls(ctx, xs, wl.dev_in, tab_ns, dtype, n)
+    errs = [_max_sigma_err(xs[r].cpu().numpy().astype(np.float64)) for r in range(min(4, len(xs)))]
+    out["newton_schulz5"] = {"value": f / (ms_ns * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms_ns, "T": wl.T,
+                             "dtype": dtype, "max_sigma_err_first4": max(errs)}
+    del xs
+    return out
+
+
+def side_line(ctx, name, args, peaks, fp32_peak, cpu_budget):
+    """Another workload, measured the same way (own roofline, e2e, CPU
+    baseline), for the ``gpt2_small`` key of the headline line."""
+    wl = load_workload(name, ctx.torch)
+    table = ctx.pe.pe_coeffs(5, wl.l, wl.T, 1.01)
+    res = measure(ctx, wl, table, "bf16", args.steps, args.warmup, peaks=peaks, fp32_peak=fp32_peak, clocks=False)
+    line = {k: res[k] for k in ("value", "ms_per_step", "us_per_muon_step_median", "us_per_poly_step", "gpu_launches",
+                                 "e2e", "roofline", "trace")}
+    line.update({"unit": "TFLOP/s", "config": {"workload": wl.name, "matrices": len(wl.shapes), "T": wl.T, "l": wl.l,
+                                               "flops_per_step": res["flops_per_step"], "note": wl.note}})
+    line["cpu_baseline"] = cpu_baseline_line(wl.host(), table, cpu_budget, wl.name)
+    line.update(small_extras(ctx, wl, table, res, "bf16", args))
+    line["torch_cublas_bf16"] = listing_line(ctx, wl, table, res["ms_per_step"], compiled=False)
+    del res["xs"]
+    return line
+
+
+def error_sweep(ctx, wl, Ts=(2, 4, 6, 8, 10, 12), gamma=1e-3):
+    """Error against the truth U V^T vs iteration count T and vs time, for the
+    Polar Express tables (FP32 plain, BF16, BF16x3) and the Newton-Schulz
+    quintic (BF16), on a workload with known factors. Errors per T: the
+    largest over the workload's matrices of max|sigma_i - 1| restricted to the
+    directions with s_i >= gamma s_max (singular values of U1^T X V1, FP64 on
+    the GPU) and of ||X - U V^T||_F / sqrt(n)."""
+    torch, pe = ctx.torch, ctx.pe
+    kept = []
+    for sv in wl.svd:
+        k = sv.s >= gamma * sv.s.max()
+        U = torch.from_numpy(sv.U).cuda()
+        V = torch.from_numpy(sv.V).cuda()
+        kept.append((U[:, k].contiguous(), V[:, k].contiguous(), U, V))
+    rows = []
+    for T in Ts:
+        for path in ("fp32", "bf16", "bf16x3", "ns5"):
+            table = np.array([NS5_ROW] * T) if path == "ns5" else pe.pe_coeffs(5, wl.l, T, 1.01)
+            dt = "bf16" if path == "ns5" else path
+            xs = [d.clone() for d in wl.dev_in]
+            ms = time_calls(ctx, xs, wl.dev_in, table, dt, 3)
+            rmax, efro = 0.0, 0.0
+            for X, (U1, V1, U, V) in zip(xs, kept):
+                Xd = X.double()
+                sig = torch.linalg.svdvals(U1.T @ Xd @ V1)
+                rmax = max(rmax, float((sig - 1).abs().max()))
+                efro = max(efro, float(torch.linalg.norm(Xd - U @ V.T) / np.sqrt(min(X.shape))))
+            rows.append({"path": path, "T": T, "ms": ms, "restricted_max_sigma_err": rmax,
+                         "err_fro_per_sqrt_n": efro})
+            del xs
+    return {"gamma": gamma, "rows": rows}
+
+
+def spectrum_bound_line(pe, wl, iters=10):
+    """Cost of the App. H bound (the power method, ``iters`` steps, on G) for
+    one matrix of each distinct shape: host wall time of the blocking call
+    (its buffers, about five launches per step and the read-back of z), and
+    z / f, which decides whether the cubic applies (z / f > 1 / sqrt 2)."""
+    seen = {}
+    for i, sh in enumerate(wl.shapes):
+        seen.setdefault(sh, i)
+    rows = []
+    for sh, i in list(seen.items())[:4]:
+        v0 = np.random.default_rng(i).standard_normal(min(sh)).astype(np.float32)
+        pe.pe_spectrum_bound(wl.dev_in[i], v0, iters)
+        t0 = time.perf_counter()
+        z, f = pe.pe_spectrum_bound(wl.dev_in[i], v0, iters)
+        rows.append({"shape": list(sh), "ms": 1e3 * (time.perf_counter() - t0), "z_over_f": z / f if f else None})
+    return {"iters": iters, "rows": rows}
+
+
+def fast_rectangular_line(ctx, n=1024, alphas=(4, 8, 32), T=6, reps=3):
+    """Alg. 4 (fast rectangular iteration, FP32 path) against the ordinary
+    FP32 iteration on n x (alpha n) Gaussian matrices, T degree-5 steps
+    (the paper's runtime comparison of restart intervals T, 3 and 1): time
+    per call with inputs resident, after an L2 flush, and its ratio."""
+    torch, pe = ctx.torch, ctx.pe
+    table = pe.pe_coeffs(5, 1e-3, T, 1.01)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(12)
+
+    def timed(fn, x, src):
+        for _ in range(2):
+            x.copy_(src)
+            fn(x)
+        tot = 0.0
+        for _ in range(reps):
+            x.copy_(src)
+            ctx.flush.fill_(5.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(ctx.stream)
+            fn(x)
+            b.record(ctx.stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / reps
+
+    rows = []
+    for al in alphas:
+        G = torch.randn(n, al * n, device="cuda", generator=gen)
+        x = G.clone()
+        base = timed(lambda t: pe.pe_polar_batched([t], table, "fp32", flags=pe.PE_BATCH_NO_GRAPH), x, G)
+        bf16 = timed(lambda t: pe.pe_polar_batched([t], table, "bf16", flags=pe.PE_BATCH_NO_GRAPH), x, G)
+        row = {"shape": [n, al * n], "alpha": al, "T": T, "fp32_ordinary_ms": base, "bf16_ordinary_ms": bf16}
+        for rs in (3, T):
+            ms = timed(lambda t: pe.pe_polar_fast_batched([t], table, restart=rs, flags=pe.PE_BATCH_NO_GRAPH), x, G)
+            row[f"fast_restart{rs}_ms"] = ms
+            row[f"speedup_restart{rs}_vs_fp32_ordinary"] = base / ms
+        rows.append(row)
+        del G, x
+    torch.cuda.empty_cache()
+    return {"path": "fp32 (SIMT) products; Gaussian inputs", "rows": rows}
+
+
+# ------------------------------------------------------------------ multi-GPU
+
+def run_sharded(ctx, wl, table, dtype, args):
+    """One set of matrices over the ranks (strong scaling): each rank owns
+    the matrices LPT assigns it and runs them in one grouped call, then one
+    all-gather gives every rank every factor (shard.polar_sharded); the
+    exchange is inside the timed region. Rank 0 prints the line."""
+    from paper_2505_16932_gb300 import shard
+    torch, pe = ctx.torch, ctx.pe
+    xs = [d.clone() for d in wl.dev_in]
+    owners = shard.assign(wl.shapes, ctx.world, len(table))
+    flops = algorithmic_flops(wl.shapes, len(table))
+
+    def step():
+        for d, s in zip(xs, wl.dev_in):
+            d.copy_(s)
+        ctx.flush.fill_(1.0)
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+        shard.polar_sharded(xs, table, dtype)
+    ctx.barrier()
+    tot = 0.0
+    for _ in range(args.steps):
+        step()
+        ctx.barrier()
+        t0 = time.perf_counter()
+        shard.polar_sharded(xs, table, dtype)
+        torch.cuda.synchronize()
+        tot += time.perf_counter() - t0
+    ms = ctx.max_over_ranks(1e3 * tot / args.steps)
+    if ctx.rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": ctx.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": wl.name, "matrices": len(wl.shapes), "T": len(table), "l": wl.l,
+                       "parallelism": f"matrices over {ctx.world} ranks (LPT), one all-gather per step",
+                       "owners": owners, "l2": "L2 flush before each step"},
+            "timing": "host wall clock between barriers, max over ranks (compute + NCCL all-gather)"}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large_dense", choices=WORKLOADS)
+    ap.add_argument("--dtype", default=None, choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--phased", action="store_true", help="three grouped launches per step")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the timed line (no comparisons, accuracy, side workload)")
+    ap.add_argument("--no-compile", action="store_true", help="skip the torch.compile run of the App. A listing")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--sweep", action="store_true",
+                    help="error vs iteration count and vs time for FP32, BF16, BF16x3 and Newton-Schulz "
+                         "(workloads with known factors)")
+    args = ap.parse_args()
+    if args.steps < 1:
+        ap.error("--steps must be >= 1")
+    args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
+
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    import paper_2505_16932_gb300 as pe
+    from paper_2505_16932_gb300 import build as B
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    B.build()
+    pe.lib()
+    ctx = Ctx(pe, torch, world, rank, local)
+    wl = load_workload(args.workload, torch)
+    dtype = args.dtype or ("fp32" if args.workload == "plain_small" else "bf16")
+    table = pe.pe_coeffs(5, wl.l, wl.T, 1.01)
+    if world > 1:
+        return run_sharded(ctx, wl, table, dtype, args)
+    peaks = measured_peaks()
+    flags = pe.PE_BATCH_PHASED if args.phased else 0
+
+    mm = None if args.no_extras else matmul_peaks(torch)
+    fp32_peak = mm["fp32_simt_tflops"] if mm else None
+    res = measure(ctx, wl, table, dtype, args.steps, args.warmup, flags, peaks, fp32_peak)
+    cpu = cpu_baseline_line(wl.host(), table, args.cpu_budget, wl.name)
+    extras = {}
+    if not args.no_extras:
+        if wl.facs is not None:
+            extras.update(large_extras(ctx, wl, table, res, dtype, peaks, mm, args))
+        else:
+            extras.update(small_extras(ctx, wl, table, res, dtype, args))
+        extras["torch_cublas_bf16"] = listing_line(ctx, wl, table, res["ms_per_step"], compiled=False)
+        extras["torch_compile_bf16"] = (listing_line(ctx, wl, table, res["ms_per_step"], compiled=True)
+                                        if not args.no_compile else {"skipped": "--no-compile"})
+        extras["matmul_peaks"] = mm
+        if args.workload == "large_dense":
+            del res["xs"]
+            extras["gpt2_small"] = side_line(ctx, "gpt2_small", args, peaks, fp32_peak, 5.0)
+            extras["spectrum_bound"] = spectrum_bound_line(pe, load_workload("gpt2_small", torch))
+        extras["fast_rectangular"] = fast_rectangular_line(ctx)
+        if args.sweep or args.workload == "ill_conditioned":
+            extras["error_vs_T"] = error_sweep(ctx, wl)
+    res.pop("xs", None)
+    line = {
+        "metric": METRIC, "value": res["value"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": wl.name, "matrices": len(wl.shapes), "T": wl.T, "l": wl.l,
+                   "path": dtype + (" grouped phased" if args.phased
+                                    else " grouped persistent (one launch per step), CUDA graph"),
+                   "flops_per_step": res["flops_per_step"],
+                   "dense_equiv_flops_per_step": dense_equiv_flops(wl.shapes, wl.T),
+                   "input_bytes": res["in_bytes"],
+                   "l2": "inputs larger than L2 and a 258 MB L2 flush before each step", "note": wl.note},
+        "us_per_muon_step": 1e3 * res["ms_per_step"],
+        "us_per_muon_step_median": res["us_per_muon_step_median"],
+        "us_per_poly_step": res["us_per_poly_step"],
+        "wall_s_timed": res["wall_s_timed"],
+        "gpu_launches": res["gpu_launches"],
+        "e2e": res["e2e"],
+        "roofline": res["roofline"],
+        "trace": res["trace"],
+        "clocks": res["clocks"],
+        "cpu_baseline": cpu,
+    }
+    line.update(extras)
+    print(json.dumps(line))
+    return 0
 
 
 if __name__ == "__main__":

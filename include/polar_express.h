@@ -200,7 +200,7 @@ int pe_sync_status(void* stream);
  * copies run asynchronously at full link bandwidth. The library keeps device
  * staging buffers per shape set (4 sets, LRU; pe_release frees them) and
  * pipelines: the matrices are cut into `ngroups` contiguous groups of about
- * equal bytes (0 = automatic: 4 for >= 8 matrices, 2 for 2-7, else 1); group
+ * equal bytes (0 = automatic: min(count, 4)); group
  * g's host->device copies run on one internal stream, its grouped compute on
  * `stream` once they have landed, its device->host copies on a second
  * internal stream, so copies in both directions overlap compute of other
@@ -387,6 +387,36 @@ int pe_split_step(pe_split_t handle, int t, const float* A, int64_t lda);
 
 /* Frees the handle's workspace (after the stream's work has finished). */
 int pe_split_close(pe_split_t handle);
+
+/* ------------------------------------ fast rectangular iteration
+ *
+ * Alg. 4 (the appendix on fast polynomial iteration for rectangular
+ * matrices) on the short side: with X the s x L normalised matrix, a block of
+ * k polynomial steps takes Y = X X^T (plus shift * I in the first block only),
+ * Q_0 = I, then per step R_t = Q_{t-1}^T Y Q_{t-1} and
+ * Q_t = Q_{t-1} (a_t I + b_t R_t + c_t R_t^2), and finally X <- Q_k X: two
+ * products with the long side per block instead of two per step. Steps run
+ * in blocks of `restart` (the appendix's restarting strategy; restart = 1 is
+ * the ordinary iteration up to the shift, restart >= T a single block).
+ * The normalisation divides by 1.01 ||G||_F + norm_eps (the appendix
+ * normalises by ||X||_F + 1e-3 with the shift).
+ *
+ * FP32 path only (dtype PE_FP32; other dtypes give PE_EUNSUPPORTED): the
+ * s x s products are grouped SIMT FP32 GEMMs. Q tends to Y^{-1/2}, so FP32
+ * rounding of Q reaches the result amplified by about the condition number of
+ * the input's normalised spectrum.
+ */
+
+/* One matrix, in place: X as for pe_polar (FP32, row-major, ld = n, device),
+ * table of T rows (a, b, c), restart in 1..64, shift = norm_eps = 1e-3 (the
+ * appendix's values), no CUDA graph. Errors: as pe_polar. */
+int pe_polar_fast(void* X, int64_t m, int64_t n, const double* table, int T, int restart, int dtype, void* stream);
+
+/* A list of matrices in one grouped launch per product: X, m, n, count as
+ * for pe_polar_batched; shift >= 0 added to Y in the first block; norm_eps
+ * >= 0; flags PE_BATCH_* (graph capture as pe_polar_batched_ex). */
+int pe_polar_fast_batched(void* const* X, const int64_t* m, const int64_t* n, int count, const double* table, int T,
+                          int restart, double shift, double norm_eps, int dtype, unsigned flags, void* stream);
 
 /* ------------------------------------ spectrum-aware initialisation
  *

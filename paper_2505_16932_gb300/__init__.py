@@ -90,6 +90,9 @@ def lib() -> ctypes.CDLL:
         "pe_split_gram": (c_i, [c_p, c_i, c_p, c_i64]),
         "pe_split_step": (c_i, [c_p, c_i, c_p, c_i64]),
         "pe_split_close": (c_i, [c_p]),
+        "pe_polar_fast": (c_i, [c_p, c_i64, c_i64, P_d, c_i, c_i, c_i, c_p]),
+        "pe_polar_fast_batched": (c_i, [ctypes.POINTER(c_p), P_i64, P_i64, c_i, P_d, c_i, c_i, c_d, c_d, c_i, c_u,
+                                        c_p]),
         "pe_spectrum_bound": (c_i, [c_p, c_i64, c_i64, ctypes.POINTER(ctypes.c_float), c_i, P_d, P_d, c_p]),
         "pe_spectrum_aware_table": (c_i, [c_d, c_d, c_d, c_i, P_d, P_d]),
         "pe_spectrum_aware_table_ex": (c_i, [c_d, c_d, c_d, c_i, c_d, c_u, P_d, P_d]),
@@ -278,6 +281,35 @@ def pe_polar_batched(Xs: Sequence, table, dtype: str = "bf16", stream=None, flag
     return Xs
 
 
+def pe_polar_fast_batched(Xs: Sequence, table, restart: int = 3, dtype: str = "fp32", shift: float = 1e-3,
+                          norm_eps: float = 1e-3, stream=None, flags: int = 0):
+    """Alg. 4 (fast rectangular iteration) in place on a list of contiguous
+    float32 CUDA matrices: blocks of ``restart`` steps, ``shift`` added to
+    Y = X X^T in the first block, normalisation by 1.01 ||G||_F + norm_eps."""
+    if len(Xs) == 0:
+        return Xs
+    for t in Xs:
+        _fp32_matrix(t)
+    n = len(Xs)
+    ptrs = (ctypes.c_void_p * n)(*[t.data_ptr() for t in Xs])
+    ms = (ctypes.c_int64 * n)(*[t.shape[0] for t in Xs])
+    ns = (ctypes.c_int64 * n)(*[t.shape[1] for t in Xs])
+    tab = _table(table)
+    _check(lib().pe_polar_fast_batched(ptrs, ms, ns, n, _dptr(tab), tab.shape[0], int(restart), float(shift),
+                                       float(norm_eps), DTYPES[dtype], int(flags),
+                                       ctypes.c_void_p(_stream_handle(stream))))
+    return Xs
+
+
+def pe_polar_fast(X, table, restart: int = 3, dtype: str = "fp32", stream=None):
+    """Alg. 4 on one contiguous float32 CUDA matrix (shift and norm_eps 1e-3)."""
+    _fp32_matrix(X)
+    tab = _table(table)
+    _check(lib().pe_polar_fast(ctypes.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], _dptr(tab), tab.shape[0],
+                               int(restart), DTYPES[dtype], ctypes.c_void_p(_stream_handle(stream))))
+    return X
+
+
 def pe_polar_batched_host(H_in: Sequence, H_out: Sequence, table, dtype: str = "bf16", ngroups: int = 0,
                           stream=None):
     """Host-buffer form: H_in / H_out are lists of contiguous float32 CPU
@@ -341,7 +373,7 @@ def pe_launch_count() -> int:
 
 
 TRACE_KINDS = ["norm_partials", "prepare", "simt_gram", "simt_square", "simt_update", "umma_step",
-               "umma_gram", "umma_square", "umma_update", "simt_gram_reduce"]
+               "umma_gram", "umma_square", "umma_update", "simt_gram_reduce", "fast_gemm", "fast_shift"]
 
 
 def pe_trace_enable(on: bool = True):

@@ -139,10 +139,15 @@ struct PlanKey {
     // fused Muon step: momentum and weight buffers per matrix (empty otherwise)
     std::vector<uintptr_t> mom, w;
     float beta = 0.f, lr = 0.f;
+    // Alg. 4 (fast rectangular iteration): steps per restart block (0: the
+    // ordinary iteration) and the first block's shift of Y
+    int restart = 0;
+    float shift = 0.f;
     bool operator==(const PlanKey& o) const {
         return dev == o.dev && dtype == o.dtype && T == o.T && io == o.io && count == o.count &&
                flags == o.flags && scale == o.scale && eps == o.eps && ptrs == o.ptrs &&
-               dims == o.dims && coef == o.coef && mom == o.mom && w == o.w && beta == o.beta && lr == o.lr;
+               dims == o.dims && coef == o.coef && mom == o.mom && w == o.w && beta == o.beta && lr == o.lr &&
+               restart == o.restart && shift == o.shift;
     }
 };
 
@@ -162,6 +167,13 @@ struct Plan {
     int n_tiles[3] = {0, 0, 0};
     TileTask* d_red = nullptr;    // SIMT: tiles of split Grams (partials summed by the reduce launch)
     int n_red = 0;
+    // Alg. 4 plans: task lists of the block's s x s products and of their
+    // split-K reductions (see enqueue_fast)
+    enum { kFSq0, kFSq1, kFP0, kFP1, kFR0, kFR1, kFH, kFQ0, kFQ1, kFLists };
+    GemmTask* d_fast[kFLists] = {};
+    int n_fast[kFLists] = {};
+    FastReduce* d_fred[kFLists] = {};
+    int n_fred[kFLists] = {};
     int* d_counters = nullptr;
     int n_counters = 0;
     UmmaPlan umma;                // tcgen05 path (tensor maps, persistent schedule)
@@ -243,7 +255,7 @@ int build_plan(const PlanKey& key, Plan** out) {
     // layout of the single workspace allocation
     const size_t o_mats = cv.take(sizeof(DevMat) * count, 64);
     std::vector<TileTask> prep, tl[3], red;
-    struct Off { size_t xf, xf2, xh0, xh1, xl0, xl1, xq, af, ah, al, bfp, bh, bl, gpart, btr; };
+    struct Off { size_t xf, xf2, xh0, xh1, xl0, xl1, xq, af, ah, al, bfp, bh, bl, gpart, btr, fq, fp, fr, fh; };
     std::vector<Off> offs(count);
     int part = 0;
     for (int i = 0; i < count; ++i) {
@@ -308,13 +320,19 @@ int build_plan(const PlanKey& key, Plan** out) {
             M.ksplit = (int32_t)((M.Lp + chunk - 1) / chunk);
             M.kchunk = (int32_t)chunk;
             if (M.ksplit > 1) o.gpart = cv.take(4 * ss * (size_t)M.ksplit);
+            if (key.restart > 0) {   // Alg. 4: Q (second buffer), P, R, H
+                o.fq = cv.take(4 * ss);
+                o.fp = cv.take(4 * ss);
+                o.fr = cv.take(4 * ss);
+                o.fh = cv.take(4 * ss);
+            }
         } else {
             o.xh0 = cv.take(2 * sL);
             o.xh1 = cv.take(2 * sL);
             o.ah = cv.take(2 * ss);
             o.bh = cv.take(2 * ss);
             if (dtype == PE_BF16) o.xq = cv.take(sL);
-            if (dtype == PE_BF16) o.btr = cv.take(4 * (size_t)(2 * (M.sp / 32)), 64);   // tr(B), tr(A) parts
+            if (dtype == PE_BF16) o.btr = cv.take(4 * (size_t)(M.sp / 32), 64);   // tr(A) parts
             if (dtype == PE_BF16 && (key.flags & kFlagSplit)) o.af = cv.take(4 * ss);   // partial Gram, FP32
             if (dtype == PE_BF16X3) {
                 o.xf = cv.take(4 * sL);
@@ -353,6 +371,36 @@ int build_plan(const PlanKey& key, Plan** out) {
     }
     P->n_red = (int)red.size();
     const size_t o_red = cv.take(sizeof(TileTask) * std::max<size_t>(1, red.size()), 64);
+    // Alg. 4: products with few output tiles are split along K (about two
+    // waves of blocks per launch; chunks of at least 128): the split factor
+    // of matrix i in a list is min(ks_list, sp_i / 128); symmetric outputs
+    // (Sq, R, H) are computed on their upper tiles
+    size_t o_fast[Plan::kFLists] = {}, o_fred[Plan::kFLists] = {};
+    std::vector<size_t> o_fpart(count, 0);
+    int ks_list[2] = {1, 1};   // [full, symmetric] products
+    auto fast_ks = [&](int i, bool sym) { return std::max(1, std::min(ks_list[sym ? 1 : 0], P->mats[i].sp / 128)); };
+    size_t fast_tasks = 0;
+    if (key.restart > 0) {
+        size_t nfull = 0, nsym = 0;
+        for (int i = 0; i < count; ++i) {
+            const size_t nt = (size_t)P->mats[i].sp / 128;
+            nfull += nt * nt;
+            nsym += nt * (nt + 1) / 2;
+        }
+        const size_t want = 2 * (size_t)std::max(1, P->ds->sms);
+        ks_list[0] = (int)std::min<size_t>(8, std::max<size_t>(1, (want + nfull - 1) / nfull));
+        ks_list[1] = (int)std::min<size_t>(8, std::max<size_t>(1, (want + nsym - 1) / nsym));
+        for (int i = 0; i < count; ++i) {
+            const size_t nt = (size_t)P->mats[i].sp / 128;
+            fast_tasks += nt * nt * (size_t)std::max(fast_ks(i, false), fast_ks(i, true));
+            const int ksm = std::max(fast_ks(i, false), fast_ks(i, true));
+            if (ksm > 1) o_fpart[i] = cv.take(sizeof(float) * (size_t)ksm * P->mats[i].sp * P->mats[i].sp);
+        }
+        for (int k = 0; k < Plan::kFLists; ++k) {
+            o_fast[k] = cv.take(sizeof(GemmTask) * fast_tasks, 64);
+            o_fred[k] = cv.take(sizeof(FastReduce) * std::max<size_t>(1, fast_tasks), 64);
+        }
+    }
     P->n_counters = 2 * count + 64;
     const size_t o_cnt = cv.take(sizeof(int) * P->n_counters, 64);
     size_t o_umma = 0, umma_bytes = 0;
@@ -408,6 +456,61 @@ int build_plan(const PlanKey& key, Plan** out) {
     P->d_prep = reinterpret_cast<TileTask*>(base + o_prep);
     for (int k = 0; k < 3; ++k) P->d_tiles[k] = reinterpret_cast<TileTask*>(base + o_tl[k]);
     P->d_red = reinterpret_cast<TileTask*>(base + o_red);
+    std::vector<GemmTask> fast_lists[Plan::kFLists];
+    std::vector<FastReduce> fred_lists[Plan::kFLists];
+    if (key.restart > 0) {
+        // Alg. 4 task lists. Q alternates between B (bfp, read by the update
+        // kernel) and fq: Q_j of a k-step block lies in Qb[(k - j) & 1], so Q_k
+        // lands in bfp. Lists by the buffer that holds the previous Q (p):
+        //   Sq[p]  Q_1 = a I + b Y + c Y Y into Qb[p]
+        //   P[p]   P = Y Qb[p]          R[p]  R = Qb[p]^T P
+        //   H      H = a I + b R + c R R  Q[p]  Qb[p ^ 1] = Qb[p] H
+        std::vector<GemmTask> lists[Plan::kFLists];
+        for (int i = 0; i < count; ++i) {
+            const DevMat& M = P->mats[i];
+            const Off& o = offs[i];
+            float* Y = reinterpret_cast<float*>(base + o.af);
+            float* Qb[2] = {reinterpret_cast<float*>(base + o.bfp), reinterpret_cast<float*>(base + o.fq)};
+            float* Pm = reinterpret_cast<float*>(base + o.fp);
+            float* R = reinterpret_cast<float*>(base + o.fr);
+            float* H = reinterpret_cast<float*>(base + o.fh);
+            const int sp = M.sp, nt = sp / 128;
+            float* part = o_fpart[i] ? reinterpret_cast<float*>(base + o_fpart[i]) : nullptr;
+            auto add = [&](int list, const float* a, const float* b, const float* e, float* c, bool sym) {
+                const int ks = fast_ks(i, sym);
+                const int chunk = (int)round_up((sp + ks - 1) / ks, 16);
+                const int nks = (sp + chunk - 1) / chunk;
+                for (int tm = 0; tm < nt; ++tm)
+                    for (int tn = sym ? tm : 0; tn < nt; ++tn) {
+                        if (nks == 1) {
+                            lists[list].push_back(
+                                GemmTask{a, b, e, c, sp, sp, sp, sp, 0, sp, tm, tn, sym ? kGemmMirror : 0, 0});
+                            continue;
+                        }
+                        for (int k = 0; k < nks; ++k)
+                            lists[list].push_back(GemmTask{a, b, nullptr, part + (size_t)k * sp * sp, sp, sp, sp, sp,
+                                                           k * chunk, std::min(chunk, sp - k * chunk), tm, tn,
+                                                           kGemmPartial, 0});
+                        fred_lists[list].push_back(
+                            FastReduce{part, e, c, (int64_t)sp * sp, nks, sp, tm, tn, sym ? kGemmMirror : 0, 0});
+                    }
+            };
+            for (int p = 0; p < 2; ++p) {
+                add(Plan::kFSq0 + p, Y, Y, Y, Qb[p], true);
+                add(Plan::kFP0 + p, Y, Qb[p], nullptr, Pm, false);
+                add(Plan::kFR0 + p, Qb[p], Pm, nullptr, R, true);
+                add(Plan::kFQ0 + p, Qb[p], H, nullptr, Qb[p ^ 1], false);
+            }
+            add(Plan::kFH, R, R, R, H, true);
+        }
+        for (int k = 0; k < Plan::kFLists; ++k) {
+            P->d_fast[k] = reinterpret_cast<GemmTask*>(base + o_fast[k]);
+            P->n_fast[k] = (int)lists[k].size();
+            P->d_fred[k] = reinterpret_cast<FastReduce*>(base + o_fred[k]);
+            P->n_fred[k] = (int)fred_lists[k].size();
+            fast_lists[k].swap(lists[k]);   // uploaded after the workspace is zeroed
+        }
+    }
     P->d_counters = reinterpret_cast<int*>(base + o_cnt);
     // zero the whole workspace once: the padding of every canonical buffer
     // stays zero from here on (prepare skips strips of padding rows), and the
@@ -424,6 +527,14 @@ int build_plan(const PlanKey& key, Plan** out) {
                              cudaMemcpyHostToDevice));
     if (!red.empty())
         PE_CU(cudaMemcpy(P->d_red, red.data(), sizeof(TileTask) * red.size(), cudaMemcpyHostToDevice));
+    for (int k = 0; k < Plan::kFLists; ++k) {
+        if (!fast_lists[k].empty())
+            PE_CU(cudaMemcpy(P->d_fast[k], fast_lists[k].data(), sizeof(GemmTask) * fast_lists[k].size(),
+                             cudaMemcpyHostToDevice));
+        if (!fred_lists[k].empty())
+            PE_CU(cudaMemcpy(P->d_fred[k], fred_lists[k].data(), sizeof(FastReduce) * fred_lists[k].size(),
+                             cudaMemcpyHostToDevice));
+    }
     PE_CU(cudaMemset(P->d_counters, 0, sizeof(int) * P->n_counters));
     if (dtype != PE_FP32) {
         const bool tune = false;   // schedules are tuned after the plan is cached (autotune)
@@ -449,6 +560,72 @@ int build_plan(const PlanKey& key, Plan** out) {
     return PE_OK;
 }
 
+// Alg. 4 (FP32 path) after prepare: the steps in blocks of k = restart (the
+// last block shorter). Per block: Y = s^2 X X^T (SIMT Gram, split-K for long
+// L; s = the normalisation factor in the first block, 1 after), the shift
+// Y += shift I in the first block, Q_1 = h_1(Y) = a I + b Y + c Y Y, then for
+// each further step P = Y Q, R = Q^T P, H = a I + b R + c R R, Q <- Q H, and
+// X <- s Q X (SIMT update kernel with a = 0 and B = Q; the last block stores
+// the caller's layout). Q_j of a k-step block is kept in Qb[(k - j) & 1]
+// (Qb[0] = DevMat::bfp, Qb[1] = the plan's second Q buffer), so Q_k is in bfp.
+int enqueue_fast(Plan* P, cudaStream_t st, int* nk) {
+    const PlanKey& k = P->key;
+    // one s x s product: its tiles (or K chunks), then the chunks' reduction
+    auto product = [&](int list, bool ta, float alpha, float beta, float gamma) -> cudaError_t {
+        cudaError_t e = launch_fast_gemm(P->d_fast[list], P->n_fast[list], ta, alpha, beta, gamma, st);
+        ++*nk;
+        if (e == cudaSuccess && P->n_fred[list]) {
+            e = launch_fast_reduce(P->d_fred[list], P->n_fred[list], alpha, beta, gamma, st);
+            ++*nk;
+        }
+        return e;
+    };
+    int cur = 0;
+    for (int t = 0; t < k.T;) {
+        const int kb = std::min(k.restart, k.T - t);
+        const bool first = (t == 0);
+        {
+            TraceScope ts(2, st);
+            PE_CU(launch_simt_phase(P->d_mats, P->d_tiles[kGram], P->n_tiles[kGram], kGram, 0.f, 0.f, 0.f, cur, 0,
+                                    first, P->d_nscale, st));
+            ++*nk;
+        }
+        if (P->n_red) {
+            TraceScope ts(9, st);
+            PE_CU(launch_simt_gram_reduce(P->d_mats, P->d_red, P->n_red, first, P->d_nscale, st));
+            ++*nk;
+        }
+        if (first && k.shift != 0.f) {
+            TraceScope ts(11, st);
+            PE_CU(launch_fast_shift(P->d_mats, (int)P->mats.size(), k.shift, st));
+            ++*nk;
+        }
+        {
+            TraceScope ts(10, st);   // the block's s x s products
+            const float a = k.coef[3 * t], b = k.coef[3 * t + 1], c = k.coef[3 * t + 2];
+            PE_CU(product(Plan::kFSq0 + ((kb - 1) & 1), false, c, b, a));
+            for (int j = 2; j <= kb; ++j) {
+                const int r = 3 * (t + j - 1);
+                const float aj = k.coef[r], bj = k.coef[r + 1], cj = k.coef[r + 2];
+                const int p = (kb - j + 1) & 1;   // the buffer holding Q_{j-1}
+                PE_CU(product(Plan::kFP0 + p, false, 1.f, 0.f, 0.f));
+                PE_CU(product(Plan::kFR0 + p, true, 1.f, 0.f, 0.f));
+                PE_CU(product(Plan::kFH, false, cj, bj, aj));
+                PE_CU(product(Plan::kFQ0 + p, false, 1.f, 0.f, 0.f));
+            }
+        }
+        {
+            TraceScope tu(4, st);
+            PE_CU(launch_simt_phase(P->d_mats, P->d_tiles[kApply], P->n_tiles[kApply], kApply, 0.f, 0.f, 0.f, cur,
+                                    t + kb == k.T, first, P->d_nscale, st));
+            ++*nk;
+        }
+        cur ^= 1;
+        t += kb;
+    }
+    return PE_OK;
+}
+
 // Enqueue the whole online stage of a plan on `st`. With `tuning`, only the
 // first min(T, 3) steps run and none of them writes the caller's buffer.
 int enqueue(Plan* P, cudaStream_t st, bool tuning = false) {
@@ -466,6 +643,12 @@ int enqueue(Plan* P, cudaStream_t st, bool tuning = false) {
                              P->d_nscale, P->ds->status, P->d_counters, P->n_counters, P->d_ticket, st));
     }
     ++nk;
+    if (k.restart > 0) {
+        const int r = enqueue_fast(P, st, &nk);
+        if (r != PE_OK) return r;
+        P->kernels_per_run = nk;
+        return PE_OK;
+    }
     const int T = tuning ? std::min(k.T, 3) : k.T;
     for (int t = 0; t < T; ++t) {
         const float a = k.coef[3 * t], b = k.coef[3 * t + 1], c = k.coef[3 * t + 2];
@@ -656,7 +839,8 @@ int get_plan(const PlanKey& key, cudaStream_t st, Plan** out, bool* fresh) {
 
 int run(void* const* X, const int64_t* m, const int64_t* n, const int64_t* ld, int count, int io,
         const double* table, int T, int dtype, double scale, double eps, unsigned flags, void* stream,
-        void* const* Mom = nullptr, void* const* W = nullptr, double beta = 0.0, double lr = 0.0) {
+        void* const* Mom = nullptr, void* const* W = nullptr, double beta = 0.0, double lr = 0.0,
+        int restart = 0, double shift = 0.0) {
     if (!X || !m || !n) return fail(PE_EINVAL, "NULL argument");
     if (count < 1 || count > kMaxMatrices) return fail(PE_EINVAL, "count must be in 1..4096");
     if (!table) return fail(PE_EINVAL, "table is NULL");
@@ -693,6 +877,13 @@ int run(void* const* X, const int64_t* m, const int64_t* n, const int64_t* ld, i
     for (int i = 0; i < 3 * T; ++i) {
         if (!std::isfinite(table[i])) return fail(PE_EINVAL, "non-finite coefficient in table");
         key.coef[i] = (float)table[i];
+    }
+    if (restart) {
+        if (restart < 1 || restart > kMaxSteps) return fail(PE_EINVAL, "restart must be in 1..64");
+        if (!(std::isfinite(shift) && shift >= 0)) return fail(PE_EINVAL, "shift must be finite and >= 0");
+        if (dtype != PE_FP32) return fail(PE_EUNSUPPORTED, "the fast rectangular iteration runs on PE_FP32");
+        key.restart = restart;
+        key.shift = (float)shift;
     }
     if (W) {
         if (!Mom) return fail(PE_EINVAL, "momentum pointer array is NULL");
@@ -835,7 +1026,7 @@ int run_host(const void* const* Hin, void* const* Hout, const int64_t* m, const 
         dims[2 * i + 1] = n[i];
         total += (size_t)(m[i] * n[i]);
     }
-    const int ng = std::min(count, ngroups > 0 ? ngroups : (count >= 8 ? 4 : (count >= 2 ? 2 : 1)));
+    const int ng = std::min(count, ngroups > 0 ? ngroups : 4);
     // contiguous groups balanced by bytes
     std::vector<int> cut(ng + 1, count);
     cut[0] = 0;
@@ -1019,6 +1210,7 @@ int split_step(Split* S, int t, const float* A, int64_t lda) {
                                     P->d_nscale, S->st));
     } else {
         PE_CU(launch_split_load_a(A, lda, S->s, M.sp, M.ah, S->st));
+        PE_CU(launch_split_d(A, lda, S->s, M.sp, M.btr, S->st));
         for (int ph = kSquare; ph <= kApply; ++ph) {
             int nl = 0;
             cudaError_t e = umma_step(&P->umma, t, a, b, c, last, ph, -1, (uint64_t)g_dbg_wait_ns, P->ds->status,
@@ -1078,6 +1270,19 @@ int pe_polar_batched_ex(void* const* X, const int64_t* m, const int64_t* n, int 
                         unsigned flags, void* stream) {
     return pe::run(X, m, n, nullptr, count, io_type, table, T, dtype, norm_scale, norm_eps, flags,
                    stream);
+}
+
+int pe_polar_fast_batched(void* const* X, const int64_t* m, const int64_t* n, int count, const double* table, int T,
+                          int restart, double shift, double norm_eps, int dtype, unsigned flags, void* stream) {
+    if (restart < 1) return pe::fail(PE_EINVAL, "restart must be in 1..64");
+    return pe::run(X, m, n, nullptr, count, PE_IO_FP32, table, T, dtype, 1.01, norm_eps, flags, stream, nullptr,
+                   nullptr, 0.0, 0.0, restart, shift);
+}
+
+int pe_polar_fast(void* X, int64_t m, int64_t n, const double* table, int T, int restart, int dtype, void* stream) {
+    void* xs[1] = {X};
+    int64_t ms[1] = {m}, ns[1] = {n};
+    return pe_polar_fast_batched(xs, ms, ns, 1, table, T, restart, 1e-3, 1e-3, dtype, PE_BATCH_NO_GRAPH, stream);
 }
 
 int pe_polar_batched_host(const void* const* Hin, void* const* Hout, const int64_t* m, const int64_t* n, int count,

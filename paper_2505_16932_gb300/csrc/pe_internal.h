@@ -63,10 +63,9 @@ struct DevMat {
     bf16* xl[2];         // BF16 X lo part (BF16x3), ping-pong
     int8_t* xq;          // BF16 path: byte of the next 8 mantissa bits of X
                          // below xh[cur] (see x_split), updated in place
-    float* btr;          // BF16 path: tr(B) of the step in sp / 32 parts, one per 32-row
-                         // diagonal chunk (written by the square epilogue, or the Gram's
-                         // when c = 0 throughout), then tr(A) in sp / 32 parts (written by
-                         // the Gram epilogue); read by the update epilogue
+    float* btr;          // BF16 path: tr(A) of the step in sp / 32 parts, one per 32-row
+                         // diagonal chunk (written by the Gram epilogue), from which the
+                         // square and update tiles compute d of the update
     int32_t ksplit;      // FP32 path: the Gram's reduction (length Lp) runs as ksplit chunks of
     int32_t kchunk;      // kchunk columns into the partial Grams gpart, summed in chunk order
                          // by the reduce kernel (ksplit <= 1: one pass straight into af)
@@ -147,14 +146,51 @@ __device__ __forceinline__ float x_join(uint32_t hi32, uint32_t cw, int k) {
     return __uint_as_float(hi32 + prmt(cw, 0u, sel) - 0x8000u);
 }
 
+// One 128 x 128 output tile of C = alpha op(A) B + beta E + gamma I (Alg. 4's
+// s x s products; E may be null): row-major operands with leading
+// dimensions, the reduction over k0 .. k0 + kn - 1 (multiples of 16).
+// flags: kGemmMirror also stores the tile transposed (a symmetric output
+// computed on its upper tiles, tm < tn); kGemmPartial stores the raw sum at
+// c (a chunk of a split reduction; a FastReduce task applies the epilogue).
+enum { kGemmMirror = 1, kGemmPartial = 2 };
+struct GemmTask {
+    const float* a;
+    const float* b;
+    const float* e;
+    float* c;
+    int32_t lda, ldb, lde, ldc;
+    int32_t k0, kn, tm, tn;
+    int32_t flags, pad0;
+};
+
+// One 128 x 128 output tile of a split reduction: C = alpha (sum of the
+// nsplit partial tiles at part + k stride, in k order) + beta E + gamma I,
+// mirrored when flags has kGemmMirror.
+struct FastReduce {
+    const float* part;
+    const float* e;
+    float* c;
+    int64_t stride;
+    int32_t nsplit, ld, tm, tn;
+    int32_t flags, pad0;
+};
+
 // ---- launchers (return cudaError_t of the launch) ----
 cudaError_t launch_prepare(const DevMat* mats, int nmats, const TileTask* tiles, int ntiles, double* partials,
                            float scale, float eps, int outputs, float* nscale, int* status, int* counters,
                            int ncounters, unsigned* ticket, cudaStream_t st);
 cudaError_t launch_split_load_a(const float* A, int64_t lda, int s, int sp, bf16* ah, cudaStream_t st);
+cudaError_t launch_split_d(const float* A, int64_t lda, int s, int sp, float* parts, cudaStream_t st);
 cudaError_t launch_simt_phase(const DevMat* mats, const TileTask* tiles, int ntiles, int kind,
                               float a, float b, float c, int src, int last, int first,
                               const float* nscale, cudaStream_t st);
+// Alg. 4 (FP32): the grouped s x s products (op(A) = A^T when ta) and the
+// first block's shift Y += shift I
+cudaError_t launch_fast_gemm(const GemmTask* tasks, int ntasks, bool ta, float alpha, float beta, float gamma,
+                             cudaStream_t st);
+cudaError_t launch_fast_reduce(const FastReduce* tasks, int ntasks, float alpha, float beta, float gamma,
+                               cudaStream_t st);
+cudaError_t launch_fast_shift(const DevMat* mats, int nmats, float shift, cudaStream_t st);
 // FP32 path, matrices with ksplit > 1: A = s^2 (sum of the partial Grams in
 // chunk order) on the tiles `tiles` (mat, tm, tn), mirrored below the diagonal
 cudaError_t launch_simt_gram_reduce(const DevMat* mats, const TileTask* tiles, int ntiles, int first,

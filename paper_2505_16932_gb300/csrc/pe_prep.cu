@@ -274,7 +274,29 @@ __global__ void __launch_bounds__(256) split_load_a_kernel(const float* __restri
     }
 }
 
+// Long-side split, BF16 path: the parts of tr(A) from which the square and
+// update tiles compute d (the fused kernel's tr_a_sum / d_of), here from the
+// summed FP32 Gram: one part per 32-row diagonal chunk, a butterfly over the
+// chunk's 32 diagonal elements (rows >= s give 0), as the Gram epilogue forms
+// them.
+__global__ void __launch_bounds__(256) split_d_kernel(const float* __restrict__ A, int64_t lda, int s, int sp,
+                                                      float* __restrict__ parts) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = warp; k < sp / 32; k += blockDim.x / 32) {
+        const int i = 32 * k + lane;
+        float d = (i < s) ? A[(int64_t)i * lda + i] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) parts[k] = d;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_split_d(const float* A, int64_t lda, int s, int sp, float* parts, cudaStream_t st) {
+    split_d_kernel<<<1, 256, 0, st>>>(A, lda, s, sp, parts);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_split_load_a(const float* A, int64_t lda, int s, int sp, bf16* ah, cudaStream_t st) {
     const int64_t n = (int64_t)sp * sp;

@@ -11,6 +11,9 @@
 //   warps 2-9  epilogue, two warpgroups (one per half of the tile's
 //              columns); each warp owns 32 tile rows (its TMEM lane quarter)
 //              and works in 32 x 32 chunks.
+//   warp 10    BF16 path: d of each square and update tile's update form,
+//              computed ahead of the epilogue and handed over in shared
+//              memory.
 // BF16 epilogue: every chunk goes TMEM -> registers -> FP32 arithmetic ->
 // swizzled shared-memory staging -> TMA bulk tensor stores; the epilogue's
 // own operand (X for the update, A for the square) is fetched ahead by TMA
@@ -53,7 +56,9 @@ namespace {
 
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = 32 * kEpiWarps;
-constexpr int kThreads = 64 + kEpiThreads;
+constexpr int kDWarp = 2 + kEpiWarps;        // computes d of the BF16 update ahead of the epilogue
+constexpr int kThreads = 64 + kEpiThreads + 32;
+constexpr int kDRing = 16;                   // d hand-off slots (full / empty barriers each)
 constexpr int kBM = 128;        // UMMA M
 constexpr int kBN = 256;        // tile width (UMMA N, <= 256)
 // The k-block BK (64 or 32 BF16 elements: one 128- or 64-byte swizzle row)
@@ -326,6 +331,40 @@ __device__ void wait_counter(const int* cnt, int target, uint64_t limit, int* st
     }
 }
 
+// The BF16 update on the compact master X, X_b its BF16 part (the MMA
+// operand): X' = (a + d) X + (B - d I) X_b, in exact arithmetic the step
+// a X + B X for every d. B - d I is what the square epilogue rounds to BF16,
+// and the update's rounding term is -(B - d I)(X - X_b). With d = 0 that term
+// does not vanish once the singular values converge and B -> (1 - a) I, and
+// the directions it rotates stay rotated. So once the mean of sigma^2,
+// m = tr(A) / s, exceeds kConvergedMeanSq, d = b m + c m^2 (the mean of B's
+// eigenvalues b sigma^2 + c sigma^4, with sigma^4 taken as m^2); before that
+// d = 0, because the small singular directions, whose later growth amplifies
+// their errors, fare better with B's own rounding.
+constexpr float kConvergedMeanSq = 0.8f;
+
+// d of the BF16 square and update (see kConvergedMeanSq) for the 64-row block
+// blk of a pack (blk = 0 otherwise), from the parts of tr(A) the Gram
+// epilogue left per 32-row diagonal chunk: lane k sums parts k, k + 32, ...
+// in index order, a butterfly adds the lanes (every lane gets the same
+// bits). The d warp computes it for each square and update tile ahead of
+// the epilogue. split_d_kernel (pe_prep.cu) leaves the same parts for the
+// long-side split.
+__device__ __forceinline__ float tr_a_sum(const DevMat& M, int blk, int lane) {
+    const int nsl = M.npack ? 2 : M.sp / 32;
+    const float* p = M.btr + blk * nsl;
+    float ta = 0.f;
+    for (int j = lane; j < nsl; j += 32) ta += __ldcg(p + j);
+    return ta;
+}
+
+__device__ __forceinline__ float d_of(float ta, const StepArgs& A, const DevMat& M) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ta += __shfl_xor_sync(0xffffffffu, ta, o);
+    const float m = ta / (float)M.s;
+    return (m > kConvergedMeanSq) ? fmaf(A.c * m, m, A.b * m) : 0.f;
+}
+
 // ------------------------------------------------------------ tile geometry
 
 // TileTask::kind carries the product in its low bits.
@@ -438,25 +477,6 @@ __device__ __forceinline__ void read_x_row(const uint8_t* buf, int r, float (&v)
         }
     }
 }
-
-// X - X_b for a decoded compact master x: its BF16 part X_b is
-// (bits(x) + 0x8000) with the low half cleared (the code adds at most
-// 0xFF00 - 0x8000 to hi << 16 and subtracts at most 0x8000), and the
-// difference of the two is exact
-__device__ __forceinline__ float x_lo(float x) {
-    return x - __uint_as_float((__float_as_uint(x) + 0x8000u) & 0xFFFF0000u);
-}
-
-// The BF16 update X' = a X + B X_b + d (X - X_b), X the compact master and
-// X_b its BF16 part (the MMA operand): in exact arithmetic this is a X + B X
-// for every d, and its rounding term is -(B - d I)(X - X_b). With d = 0 (the
-// plain a X + B X_b) that term does not vanish once the singular values
-// converge and B -> (1 - a) I, and the directions it rotates stay rotated;
-// d = tr(B) / s gives the term its smallest Frobenius norm, but early on it
-// hurts the small singular directions, whose later growth amplifies it. So
-// d = tr(B) / s once the mean of sigma^2, tr(A) / s, exceeds
-// kConvergedMeanSq, else d = 0.
-constexpr float kConvergedMeanSq = 0.8f;
 
 // sum over the warp of each lane's element v[lane] (the diagonal of a
 // diagonal chunk); every lane gets the same bits (xor butterfly)
@@ -640,7 +660,7 @@ struct Cfg {
     static constexpr int kEpiOff = kStages * kStage;
     static constexpr int kBarOff = kEpiOff + ((NS == 1) ? kEpiWarps * kWarpStage : 0);
     static_assert(kWarpStage % 1024 == 0, "staging boxes need 1024-byte alignment");
-    static constexpr size_t kSmem = 1024 + kBarOff + 512;
+    static constexpr size_t kSmem = 1024 + kBarOff + 1024;   // barriers, TMEM slot, d ring
 };
 
 // Per-role cycle counters (debug profiling), slot k of CTA b at prof[32 b + k].
@@ -664,6 +684,12 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
     using C = Cfg<NS, BK, MODE>;
     static_assert(MODE == 0 || MODE == 2, "kernel modes: 0 (1-SM tiles) and 2 (2-SM UMMA)");
     constexpr bool kCg2 = (MODE == 2);
+    // the BF16 update's d (see kConvergedMeanSq): computed by the square and
+    // update tiles from parts of tr(A) that the Gram tiles write, or, for the
+    // long-side split (GF32), whose Grams are partial, split_d_kernel from the
+    // summed Gram
+    constexpr bool kUseD = (NS == 1);
+    constexpr bool kPubD = (NS == 1) && !GF32;
     constexpr int kCols = 256 * NACC;
     constexpr int kABytes = C::kABytes;
     constexpr int kBBytes = C::kBBytes;
@@ -678,6 +704,9 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
     uint64_t* pfbar = drain + 1;            // two operand-prefetch barriers per epilogue warp
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pfbar + 2 * kEpiWarps);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    uint64_t* dfull = reinterpret_cast<uint64_t*>(tmem_slot + 2);   // d ring: slot written
+    uint64_t* dempty = dfull + kDRing;                              // d ring: slot read by every epilogue warp
+    float* dring = reinterpret_cast<float*>(dempty + kDRing);       // kDRing x 4 (a value per 64-row block)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t limit = A.wait_ns ? A.wait_ns : kDefaultWaitNs;
@@ -701,6 +730,10 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
         }
         mbar_init(drain, 1);
         for (int w = 0; w < 2 * kEpiWarps; ++w) mbar_init(&pfbar[w], 1);
+        for (int k = 0; k < kDRing; ++k) {
+            mbar_init(&dfull[k], 1);
+            mbar_init(&dempty[k], kEpiWarps);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
@@ -881,6 +914,45 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             prof[kPTEmptyWait] += c_tempty;
             prof[kPMma] += clock64() - k_t0;
         }
+    } else if (warp == kDWarp) {
+        // ------------------------------------------------------ d of the BF16 update
+        // Walks the CTA's tile list ahead of the epilogue: for each square and
+        // update tile, once its matrix's Gram is complete (parts of tr(A)), d
+        // per 64-row block of this CTA's rows into a ring slot; the epilogue
+        // frees the slot after reading it.
+        if (kUseD) {
+            int slot = 0;
+            uint32_t ph = 0;
+            for (int it = t_begin; it < t_end; ++it) {
+                const TileTask tk = PE_TILE(it);
+                const DevMat& M = A.mats[tk.mat];
+                if ((tk.kind & kKindMask) == kGram || !M.btr || A.cubic) continue;
+                if (!mbar_wait(&dempty[slot], ph ^ 1, limit, abort_flag)) {
+                    if (lane == 0) {
+                        *abort_flag = 1;
+                        atomicOr(A.status, 4);
+                    }
+                    break;
+                }
+                if (A.dependent) {   // the parts come from other CTAs' Gram tiles
+                    const int* cnt = A.counters + 2 * tk.mat;
+                    if (lane == 0) wait_counter(cnt, (A.step + 1) * A.need[2 * tk.mat], limit, A.status);
+                    __syncwarp();
+                    (void)ld_acquire(cnt);
+                }
+                const int row0 = kCg2 ? tk.tm * 2 * kBM + crank * kBM : tk.tm * kBM;
+                for (int j = 0; j < (M.npack ? kBM / 64 : 1); ++j) {
+                    const float dj = d_of(tr_a_sum(M, M.npack ? (row0 >> 6) + j : 0, lane), A, M);
+                    if (lane == 0) dring[4 * slot + j] = dj;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&dfull[slot]);
+                if (++slot == kDRing) {
+                    slot = 0;
+                    ph ^= 1;
+                }
+            }
+        }
     } else if (warp >= 2) {
         // ------------------------------------------------------ epilogue
         const int ew = warp - 2;           // 0..7
@@ -899,6 +971,8 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
         uint32_t pf_issued = 0, pf_used = 0;
         int acc = 0;
         uint32_t acc_phase = 0;
+        int dslot = 0;         // d ring slot of the next square / update tile
+        uint32_t dph = 0;
         long long c_tfull = 0, c_dep = 0, c_gram = 0, c_sq = 0, c_ap = 0, c_rdx = 0, c_pf = 0, c_math = 0, c_st = 0, c_fn = 0,
                   c_is = 0, c_tm = 0;
         for (int it = t_begin; it < t_end; ++it) {
@@ -930,6 +1004,9 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                 }
                 c_dep += clock64() - c0;
             }
+            // BF16 square and update: d comes from the d warp's ring (not for
+            // c = 0 tables, whose B comes from the Gram)
+            const bool use_d = kUseD && (g.kind != kGram) && M.btr && !A.cubic;
             // first chunk that this warp stores (symmetric outputs skip lower chunks)
             int first = 0;
             if (sym) {
@@ -970,36 +1047,21 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             const long long c1 = clock64();
             c_tfull += c1 - c0;
             const uint32_t tbase = tmem_base + acc * 256 + ((uint32_t)(q * 32) << 16) + grp * nch * 32;
-            // BF16 update: d of the update (see kConvergedMeanSq) from the
-            // parts of tr(B) and tr(A) the square and Gram epilogues left per
-            // 32-row diagonal chunk, each summed in a fixed order (lane k takes
-            // parts k, k + 32, ..., then a butterfly); the parts of a pack's
-            // 64-row block k are 2k and 2k + 1
             float dtr = 0.f;
-            if (NS == 1 && g.kind == kApply && M.btr) {
-                if (A.dependent) {   // the parts come from other CTAs: acquire their releases
-                    const int which = A.cubic ? 0 : 1;
-                    const int* cnt = A.counters + 2 * g.mat + which;
-                    if (lane == 0) wait_counter(cnt, (A.step + 1) * A.need[2 * g.mat + which], limit, A.status);
-                    __syncwarp();
-                    (void)ld_acquire(cnt);
-                    (void)ld_acquire(A.counters + 2 * g.mat);   // the Gram's (tr(A) parts)
+            if (use_d) {
+                if (!mbar_wait(&dfull[dslot], dph, limit, abort_flag)) {
+                    *abort_flag = 1;
+                    atomicOr(A.status, 4);
+                    break;
                 }
-                const int nsl = M.npack ? 2 : M.sp / 32;
-                const float* slb = M.btr + (M.npack ? 2 * (gi0 >> 6) : 0);
-                const float* sla = slb + M.sp / 32;
-                float tb = 0.f, ta = 0.f;
-                for (int k = lane; k < nsl; k += 32) {
-                    tb += __ldcg(slb + k);
-                    ta += __ldcg(sla + k);
+                const int row0 = kCg2 ? tk.tm * 2 * kBM + crank * kBM : tk.tm * kBM;
+                dtr = dring[4 * dslot + (M.npack ? (gi0 >> 6) - (row0 >> 6) : 0)];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&dempty[dslot]);
+                if (++dslot == kDRing) {
+                    dslot = 0;
+                    dph ^= 1;
                 }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    tb += __shfl_xor_sync(0xffffffffu, tb, o);
-                    ta += __shfl_xor_sync(0xffffffffu, ta, o);
-                }
-                if (A.cubic) ta = (A.b != 0.f) ? tb / A.b : 0.f;   // B = b A
-                if (ta > kConvergedMeanSq * (float)M.s) dtr = tb / (float)M.s;
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -1038,29 +1100,31 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                         }
                     }
                     if (g.kind == kApply) {
-                        // X' = a X + B X_b + d (X - X_b) (see x_lo)
+                        // X' = (a + d) X + (B - d I) X_b (see kConvergedMeanSq)
+                        const float ad = A.a + dtr;
                         if (A.step == 0) {
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) v[j] = s0 * fmaf(dtr, x_lo(pre[j]), fmaf(A.a, pre[j], v[j]));
+                            for (int j = 0; j < 32; ++j) v[j] = s0 * fmaf(ad, pre[j], v[j]);
                         } else {
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) v[j] = fmaf(dtr, x_lo(pre[j]), fmaf(A.a, pre[j], v[j]));
+                            for (int j = 0; j < 32; ++j) v[j] = fmaf(ad, pre[j], v[j]);
                         }
                     } else if (g.kind == kSquare) {
 #pragma unroll
                         for (int j = 0; j < 32; ++j) v[j] = fmaf(A.b, pre[j], A.c * v[j]);
-                        if (M.btr && cls == kChunkDiag) {
-                            const float dg = warp_diag_sum(v, lane);
-                            if (lane == 0) M.btr[gi0 >> 5] = dg;
+                        if (use_d && cls == kChunkDiag) {   // B - d I
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                if (j == lane) v[j] -= dtr;
                         }
                     } else {
                         // Gram: A = s^2 X X^T, or B = b s^2 X X^T when c = 0 throughout
                         const float gs = A.cubic ? A.b * s0 * s0 : s0 * s0;
 #pragma unroll
                         for (int j = 0; j < 32; ++j) v[j] *= gs;
-                        if (M.btr && cls == kChunkDiag) {   // tr(B) parts (c = 0), else tr(A) parts
+                        if (kPubD && M.btr && !A.cubic && cls == kChunkDiag) {   // the parts of tr(A)
                             const float dg = warp_diag_sum(v, lane);
-                            if (lane == 0) M.btr[(A.cubic ? 0 : M.sp / 32) + (gi0 >> 5)] = dg;
+                            if (lane == 0) M.btr[gi0 >> 5] = dg;
                         }
                     }
                     if (sub) { const long long t = clock64(); c_rdx += t - s0c; s0c = t; }
