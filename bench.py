@@ -913,6 +913,50 @@ def run_sharded(ctx, wl, table, dtype, args):
 
 # ------------------------------------------------------------------ main
 
+def role_cycles(ctx, wl, table, dtype):
+    """Per-role cycle counters of the tcgen05 step kernel (debug key 4) over
+    one grouped call, as fractions of the kernel's own cycles, averaged over
+    the persistent CTAs: where the producer, MMA and epilogue warps spend their
+    time (a diagnostic, printed instead of the bench line)."""
+    torch, pe = ctx.torch, ctx.pe
+    xs = [m.clone() for m in wl.dev_in]
+    src = [x.clone() for x in xs]
+    for _ in range(3):
+        for d, s in zip(xs, src):
+            d.copy_(s)
+        pe.pe_polar_batched(xs, table, dtype)
+    torch.cuda.synchronize()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    prof = torch.zeros(32 * 4096, dtype=torch.int64, device="cuda")
+    pe.pe_debug_set(4, prof.data_ptr())
+    try:
+        for d, s in zip(xs, src):
+            d.copy_(s)
+        pe.pe_polar_batched(xs, table, dtype)
+        torch.cuda.synchronize()
+    finally:
+        pe.pe_debug_set(4, 0)
+    pe.pe_sync_status()
+    P = prof.view(4096, 32)[:nsm].double().cpu().numpy()
+    names = {0: "total", 11: "producer", 1: "producer_wait_dependency", 2: "producer_wait_free_stage",
+             12: "mma", 3: "mma_wait_operands", 4: "mma_wait_free_accumulator",
+             5: "epilogue_wait_accumulator", 9: "epilogue_wait_dependency", 6: "epilogue_gram_tiles",
+             7: "epilogue_square_tiles", 8: "epilogue_update_tiles", 18: "update_tmem_load",
+             14: "update_wait_prefetched_operand", 13: "update_operand_read_and_arithmetic",
+             10: "update_wait_output_box", 15: "update_output_staging", 16: "update_proxy_fence",
+             17: "update_store_and_prefetch_issue"}
+    tot = P[:, 0].mean()
+    # 2-SM UMMA: only the even CTA of a pair issues MMAs, so the MMA slots
+    # average over the CTAs that recorded any
+    issuers = P[:, 12] > 0
+    frac = {}
+    for k, v in names.items():
+        rows = P[issuers, k] if k in (3, 4, 12) and issuers.any() else P[:, k]
+        frac[v] = float(rows.mean() / tot)
+    return {"workload": wl.name, "dtype": dtype, "ctas": nsm, "mma_issuing_ctas": int(issuers.sum()),
+            "fractions_of_kernel_cycles": frac}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -929,6 +973,8 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="error vs iteration count and vs time for FP32, BF16, BF16x3 and Newton-Schulz "
                          "(workloads with known factors)")
+    ap.add_argument("--role-cycles", action="store_true",
+                    help="print the step kernel's per-role cycle fractions (debug counters) instead of timing")
     args = ap.parse_args()
     if args.steps < 1:
         ap.error("--steps must be >= 1")
@@ -954,6 +1000,9 @@ def main():
     table = pe.pe_coeffs(5, wl.l, wl.T, 1.01)
     if world > 1:
         return run_sharded(ctx, wl, table, dtype, args)
+    if args.role_cycles:
+        print(json.dumps(role_cycles(ctx, wl, table, dtype)))
+        return 0
     peaks = measured_peaks()
     flags = pe.PE_BATCH_PHASED if args.phased else 0
 
