@@ -257,7 +257,9 @@ void pe_release(void);
  *          2/3/4 lagged interleave of phases across matrices (lag 4/8/16).
  *   key 7: kernel mode of tcgen05 plans built from now on (-1 = autotuned,
  *          0 = one CTA per 128x256 tile, 2 = 2-SM UMMA on 256x256 tiles when
- *          every size is a multiple of 256); any other value is PE_EINVAL.
+ *          every size is a multiple of 256, 3 = mode 2 with twelve epilogue
+ *          warps and four operand stages instead of eight and five); any other
+ *          value is PE_EINVAL.
  *   key 8: accumulators per CTA of 2-SM plans built from now on (1 or 2;
  *          0 = default).
  *   key 9: value != 0 turns off the pairing of BF16 matrices with a short

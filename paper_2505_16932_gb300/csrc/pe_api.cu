@@ -758,7 +758,8 @@ int autotune(Plan* P, cudaStream_t st) {
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
         const int mode = it->second / 16, order = it->second % 16;
-        if ((mode != 0 && mode != 2) || (mode == 2 && P->umma.max_clusters2 < 1))
+        if ((mode != 0 && mode != 2 && mode != 3) || (mode == 2 && P->umma.max_clusters2 < 1) ||
+            (mode == 3 && P->umma.max_clusters3 < 1))
             return PE_OK;   // cached on another configuration
         P->umma.mode = mode;
         return umma_schedule(&P->umma, order, &g_err);
@@ -775,6 +776,7 @@ int autotune(Plan* P, cudaStream_t st) {
     else {
         modes.push_back(0);
         if (P->umma.max_clusters2 > 0) modes.push_back(2);
+        if (P->umma.max_clusters3 > 0) modes.push_back(3);
     }
     // Round robin over the candidates (a warm-up pass, then two timed passes,
     // the faster run of each candidate counts), so that a drift of clocks or
@@ -1409,7 +1411,8 @@ int pe_debug_set(int key, int64_t value) {
         case 5: pe::g_dbg_bk = (int)value; return PE_OK;
         case 6: pe::g_dbg_order = (int)value; return PE_OK;
         case 7:
-            if (value != -1 && value != 0 && value != 2) return pe::fail(PE_EINVAL, "kernel mode must be -1, 0 or 2");
+            if (value != -1 && value != 0 && value != 2 && value != 3)
+                return pe::fail(PE_EINVAL, "kernel mode must be -1, 0, 2 or 3");
             pe::g_dbg_mode = (int)value;
             return PE_OK;
         case 8: pe::g_dbg_nacc = (int)value; return PE_OK;

@@ -54,10 +54,9 @@
 namespace pe {
 namespace {
 
-constexpr int kEpiWarps = 8;
-constexpr int kEpiThreads = 32 * kEpiWarps;
-constexpr int kDWarp = 2 + kEpiWarps;        // computes d of the BF16 update ahead of the epilogue
-constexpr int kThreads = 64 + kEpiThreads + 32;
+// Block layout: warp 0 producer, warp 1 MMA, then EW epilogue warps (8, or 12
+// in the 2-SM kernel variant with more epilogue warps), then the d warp.
+constexpr int threads_of(int ew) { return 64 + 32 * ew + 32; }
 constexpr int kDRing = 16;                   // d hand-off slots (full / empty barriers each)
 constexpr int kBM = 128;        // UMMA M
 constexpr int kBN = 256;        // tile width (UMMA N, <= 256)
@@ -311,7 +310,9 @@ __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// named barrier of the N epilogue threads
+template <int N>
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory"); }
 
 // Bounded wait for a readiness counter (fused mode). On expiry the status
 // word records a timeout and the caller proceeds: the launch always ends,
@@ -643,13 +644,18 @@ __device__ __forceinline__ void chunk_hl(const Geo& g, const DevMat& M, const St
 // MODE 0: one CTA per 128 x 256 tile. MODE 2: 2-SM UMMA (cta_group::2) on
 // 256 x 256 tiles, each CTA holding half of A (its 128 rows) and half of B
 // (128 of the 256 columns). (MODE 1 is not used.)
-template <int NS, int BK, int MODE = 0>
+template <int NS, int BK, int MODE = 0, int EW = 8>
 struct Cfg {
+    static constexpr int kEpiWarps = EW;
+    static constexpr int kEpiThreads = 32 * EW;
+    static constexpr int kDWarp = 2 + EW;   // computes d of the BF16 update ahead of the epilogue
+    static constexpr int kThreads = threads_of(EW);
     static constexpr int kABytes = kBM * BK * 2;      // A tile of one k-block
     static constexpr int kBBytes = ((MODE == 2) ? kBN / 2 : kBN) * BK * 2;   // B tile (or half) of one k-block
     static constexpr int kAOps = (NS == 1) ? 1 : 2;   // stage: A hi | [A lo] | B hi | [B lo]
     static constexpr int kStage = kAOps * (kABytes + kBBytes);
-    static constexpr int kStages = (MODE == 2) ? 5 : ((NS == 1) ? 3 : 2) * (64 / BK);
+    // (twelve epilogue warps take the shared memory of a fifth stage)
+    static constexpr int kStages = (MODE == 2) ? (EW == 8 ? 5 : 4) : ((NS == 1) ? 3 : 2) * (64 / BK);
     // BF16 epilogue staging per warp: operand prefetch buffers of 3 KB (two,
     // fetched two chunks ahead; one in the 2-SM kernel, whose smem goes to a
     // fifth operand stage) and a 4 KB output box
@@ -658,7 +664,7 @@ struct Cfg {
     static constexpr uint32_t kSwzK = (BK == 64) ? 2u : 4u;   // K-major operand swizzle
     static constexpr uint32_t kSboK = 8 * BK * 2;             // 8 rows of one k-block
     static constexpr int kEpiOff = kStages * kStage;
-    static constexpr int kBarOff = kEpiOff + ((NS == 1) ? kEpiWarps * kWarpStage : 0);
+    static constexpr int kBarOff = kEpiOff + ((NS == 1) ? EW * kWarpStage : 0);
     static_assert(kWarpStage % 1024 == 0, "staging boxes need 1024-byte alignment");
     static constexpr size_t kSmem = 1024 + kBarOff + 1024;   // barriers, TMEM slot, d ring
 };
@@ -679,9 +685,12 @@ enum ProfSlot {
 // columns are allocated (two give epilogue / MMA overlap).
 // GF32: the long-side split's kernel, whose Gram writes the full FP32 A
 // (DevMat::af); a separate instantiation keeps that path out of the others.
-template <int NS, int BK, int MODE, int NACC, bool GF32 = false>
-__global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_constant__ StepArgs A) {
-    using C = Cfg<NS, BK, MODE>;
+template <int NS, int BK, int MODE, int NACC, bool GF32 = false, int EW = 8>
+__global__ void __launch_bounds__(threads_of(EW), 1) umma_step_kernel(const __grid_constant__ StepArgs A) {
+    using C = Cfg<NS, BK, MODE, EW>;
+    static_assert(EW == 8 || (EW == 12 && NS == 1 && MODE == 2 && !GF32), "epilogue warps: 8, or 12 (2-SM BF16)");
+    constexpr int kEpiWarps = C::kEpiWarps;
+    constexpr int kEpiThreads = C::kEpiThreads;
     static_assert(MODE == 0 || MODE == 2, "kernel modes: 0 (1-SM tiles) and 2 (2-SM UMMA)");
     constexpr bool kCg2 = (MODE == 2);
     // the BF16 update's d (see kConvergedMeanSq): computed by the square and
@@ -914,7 +923,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             prof[kPTEmptyWait] += c_tempty;
             prof[kPMma] += clock64() - k_t0;
         }
-    } else if (warp == kDWarp) {
+    } else if (warp == C::kDWarp) {
         // ------------------------------------------------------ d of the BF16 update
         // Walks the CTA's tile list ahead of the epilogue: for each square and
         // update tile, once its matrix's Gram is complete (parts of tr(A)), d
@@ -955,9 +964,13 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
         }
     } else if (warp >= 2) {
         // ------------------------------------------------------ epilogue
-        const int ew = warp - 2;           // 0..7
+        const int ew = warp - 2;           // 0 .. EW - 1
         const int q = warp & 3;            // TMEM lane quarter = the warp's 32 tile rows
-        const int grp = ew >> 2;           // column half of the tile
+        const int grp = ew >> 2;           // column group of the tile (EW / 4 groups)
+        constexpr int kGroups = EW / 4;
+        // 32-column chunks per warp: 8 warps take a contiguous half of the
+        // tile row each, 12 take every third chunk
+        constexpr int kMaxCh = (kBN / 32 + kGroups - 1) / kGroups;
         const int etid = threadIdx.x - 64; // 0..255
         constexpr int NPF = C::kNpf;
         uint8_t* stg = smem + C::kEpiOff + ew * C::kWarpStage;
@@ -983,8 +996,10 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             // the warp's first row (2-SM: this CTA holds rows 128 crank .. of the 256-row tile)
             const int gi0 = (kCg2 ? tk.tm * 2 * kBM + crank * kBM : g.tm * kBM) + q * 32;
             const int gi = gi0 + lane;
-            const int nch = g.bn / 64;              // 32-column chunks per warpgroup
-            const int cb = g.col0 + grp * nch * 32; // the warpgroup's first column
+            // this warp's chunks: columns cb + i cs, i < nch
+            const int nch = (kGroups == 2) ? g.bn / 64 : (g.bn / 32 - grp + kGroups - 1) / kGroups;
+            const int cb = g.col0 + ((kGroups == 2) ? grp * nch * 32 : grp * 32);
+            constexpr int cs = (kGroups == 2) ? 32 : 32 * kGroups;
             const bool sym = (g.kind != kApply);
             const bool needs_in = (g.kind != kGram);
             // step 0 runs on the unscaled prepared X and applies the
@@ -1010,7 +1025,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             // first chunk that this warp stores (symmetric outputs skip lower chunks)
             int first = 0;
             if (sym) {
-                while (first < nch && chunk_class(gi0, cb + first * 32) == kChunkLower) ++first;
+                while (first < nch && chunk_class(gi0, cb + first * cs) == kChunkLower) ++first;
             }
             float pre[32];
             const float* in_g = (NS == 1) ? nullptr
@@ -1024,8 +1039,8 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                 if (lane == 0) {
                     const uint32_t dst = smem_u32(s_pf + b * 3072);
                     mbar_expect_tx(&pfbar[2 * ew + b], in_bytes);
-                    tma_load_2d(dst, in_map, &pfbar[2 * ew + b], cb + ch * 32, gi0);
-                    if (g.kind == kApply) tma_load_2d(dst + 2048, mp + kMapEXQ, &pfbar[2 * ew + b], cb + ch * 32, gi0);
+                    tma_load_2d(dst, in_map, &pfbar[2 * ew + b], cb + ch * cs, gi0);
+                    if (g.kind == kApply) tma_load_2d(dst + 2048, mp + kMapEXQ, &pfbar[2 * ew + b], cb + ch * cs, gi0);
                 }
                 ++pf_issued;
             };
@@ -1035,7 +1050,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                     if (NPF == 2 && first + 1 < nch) prefetch(first + 1);
                 }
             } else if (needs_in && first < nch) {
-                load32(pre, in_g + cb + first * 32);
+                load32(pre, in_g + cb + first * cs);
             }
             long long c0 = clock64();
             if (!mbar_wait(&tfull[acc], acc_phase, limit, abort_flag)) {
@@ -1046,7 +1061,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
             tc_fence_after();
             const long long c1 = clock64();
             c_tfull += c1 - c0;
-            const uint32_t tbase = tmem_base + acc * 256 + ((uint32_t)(q * 32) << 16) + grp * nch * 32;
+            const uint32_t tbase = tmem_base + acc * 256 + ((uint32_t)(q * 32) << 16) + (cb - g.col0);
             float dtr = 0.f;
             if (use_d) {
                 if (!mbar_wait(&dfull[dslot], dph, limit, abort_flag)) {
@@ -1064,9 +1079,9 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                 }
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < kMaxCh; ++i) {
                 if (i >= nch || i < first) continue;
-                const int col0 = cb + i * 32;
+                const int col0 = cb + i * cs;
                 const int cls = sym ? chunk_class(gi0, col0) : kChunkUpper;
                 if (cls == kChunkLower) continue;
                 // pack: the Gram's blocks between different matrices stay zero
@@ -1075,11 +1090,11 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                 // next stored chunk (for the prefetch)
                 int nx = i + 1;
                 if (sym)
-                    while (nx < nch && chunk_class(gi0, cb + nx * 32) == kChunkLower) ++nx;
+                    while (nx < nch && chunk_class(gi0, cb + nx * cs) == kChunkLower) ++nx;
                 float v[32];
                 const bool sub = prof && g.kind == kApply;   // debug: update epilogue sub-steps
                 long long s0c = sub ? clock64() : 0;
-                tmem_ld32(tbase + i * 32, v);
+                tmem_ld32(tbase + i * cs, v);
                 if (sub) { const long long t = clock64(); c_tm += t - s0c; s0c = t; }
                 if (NS == 1) {
                     if (needs_in) {
@@ -1202,7 +1217,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                     if (sub) { __syncwarp(); c_is += clock64() - s0c; }
                 } else {
                     float nxt_pre[32];
-                    if (needs_in && nx < nch) load32(nxt_pre, in_g + cb + nx * 32);
+                    if (needs_in && nx < nch) load32(nxt_pre, in_g + cb + nx * cs);
                     chunk_hl(g, M, A, gi, col0, cls, s0, v, pre);
                     if (needs_in && nx < nch) {
 #pragma unroll
@@ -1224,7 +1239,7 @@ __global__ void __launch_bounds__(kThreads, 1) umma_step_kernel(const __grid_con
                     fence_proxy_async_global();
                 }
                 __threadfence();
-                epi_bar();
+                epi_bar<kEpiThreads>();
                 if (etid == 0 && !(g.kind == kGram && g.mat == A.withhold))
                     red_release_add(A.counters + 2 * g.mat + (g.kind == kSquare ? 1 : 0), 1);
             }
@@ -1437,7 +1452,7 @@ void lpt_units(const std::vector<Unit>& order, int groups, std::vector<int>* off
 }  // namespace
 
 int umma_schedule(UmmaPlan* P, int order, std::string* err) {
-    const bool cg2 = P->mode == 2;     // one 256 x 256 tile per unit
+    const bool cg2 = P->mode >= 2;     // one 256 x 256 tile per unit
     const int inphase = (order == 1) ? 1 : 0;
     std::vector<Unit> ph[3];
     for (int k = 0; k < 3; ++k) {
@@ -1467,7 +1482,7 @@ int umma_schedule(UmmaPlan* P, int order, std::string* err) {
         });
         for (const Keyed& k : all) fused.push_back(ph[k.phase][k.pos]);
     }
-    const int cap = cg2 ? P->max_clusters2 : P->sms;   // scheduling groups
+    const int cap = (P->mode == 3) ? P->max_clusters3 : cg2 ? P->max_clusters2 : P->sms;   // scheduling groups
     P->ntiles = (int)fused.size();
     const int groups = std::max(1, std::min(cap, P->ntiles));
     P->grid = cg2 ? 2 * groups : groups;
@@ -1622,6 +1637,7 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
     if (P->nsplit == 3) P->smem_bytes = (P->bk == 64) ? Cfg<3, 64>::kSmem : Cfg<3, 32>::kSmem;
     else P->smem_bytes = (P->bk == 64) ? Cfg<1, 64>::kSmem : Cfg<1, 32>::kSmem;
     P->smem_bytes2 = Cfg<1, 64, 2>::kSmem;
+    P->smem_bytes3 = Cfg<1, 64, 2, 12>::kSmem;
     e = cudaFuncSetAttribute(umma_step_kernel<1, 64, 0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Cfg<1, 64>::kSmem);
     if (e == cudaSuccess)
@@ -1642,6 +1658,7 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
     }
     // 2-SM UMMA: 256 x 256 tiles, needs every padded size to be a multiple of 256
     P->max_clusters2 = 0;
+    P->max_clusters3 = 0;
     bool even = (P->nsplit == 1 && P->bk == 64);
     for (int i = 0; i < count && even; ++i) even = (mats[i].sp % 256 == 0) && (mats[i].Lp % 256 == 0);
     if (even) {
@@ -1675,13 +1692,16 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(umma_step_kernel<1, 64, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)Cfg<1, 64, 2>::kSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(umma_step_kernel<1, 64, 2, 2, false, 12>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg<1, 64, 2, 12>::kSmem);
         if (e == cudaSuccess && P->need2)
             e = cudaMemcpy(P->need2, need2.data(), sizeof(int) * need2.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess && P->need2) {
             cudaLaunchConfig_t cfg;
             memset(&cfg, 0, sizeof(cfg));
             cfg.gridDim = dim3(2 * (sms / 2));
-            cfg.blockDim = dim3(kThreads);
+            cfg.blockDim = dim3(Cfg<1, 64, 2>::kThreads);
             cfg.dynamicSmemBytes = Cfg<1, 64, 2>::kSmem;
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1693,10 +1713,17 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
             int n = 0;
             if (cudaOccupancyMaxActiveClusters(&n, umma_step_kernel<1, 64, 2, 2>, &cfg) == cudaSuccess)
                 P->max_clusters2 = std::min(n, sms / 2);
+            // the variant with twelve epilogue warps (mode 3)
+            cfg.blockDim = dim3(Cfg<1, 64, 2, 12>::kThreads);
+            cfg.dynamicSmemBytes = Cfg<1, 64, 2, 12>::kSmem;
+            n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, umma_step_kernel<1, 64, 2, 2, false, 12>, &cfg) == cudaSuccess)
+                P->max_clusters3 = std::min(n, sms / 2);
         }
         cudaGetLastError();
     }
-    if (P->mode != 0 && P->mode != 2) P->mode = 0;
+    if (P->mode != 0 && P->mode != 2 && P->mode != 3) P->mode = 0;
+    if (P->mode == 3 && P->max_clusters3 < 1) P->mode = 2;
     if (P->mode == 2 && P->max_clusters2 < 1) P->mode = 0;
     return umma_schedule(P, P->order, err);
 }
@@ -1707,7 +1734,7 @@ cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, i
     A.nscale = P->nscale;
     A.mats = P->d_mats;
     A.maps = reinterpret_cast<const CUtensorMap*>(P->maps);
-    A.need = (P->mode == 2) ? P->need2 : P->need;
+    A.need = (P->mode >= 2) ? P->need2 : P->need;
     A.counters = P->counters;
     A.status = status;
     A.a = a;
@@ -1726,8 +1753,8 @@ cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, i
         cudaLaunchConfig_t cfg;
         memset(&cfg, 0, sizeof(cfg));
         cfg.gridDim = dim3(grid);
-        cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = (P->mode == 2) ? P->smem_bytes2 : P->smem_bytes;
+        cfg.blockDim = dim3((P->mode == 3) ? Cfg<1, 64, 2, 12>::kThreads : Cfg<1, 64>::kThreads);
+        cfg.dynamicSmemBytes = (P->mode == 3) ? P->smem_bytes3 : (P->mode == 2) ? P->smem_bytes2 : P->smem_bytes;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         if (P->mode != 0) {
@@ -1749,6 +1776,7 @@ cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, i
             return cudaLaunchKernelEx(&cfg, umma_step_kernel<3, 32, 0, 2>, A);
         }
         if (P->gram_f32) return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64, 0, 2, true>, A);
+        if (P->mode == 3) return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64, 2, 2, false, 12>, A);
         if (P->mode == 2) {
             if (P->nacc == 2) return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64, 2, 2>, A);
             return cudaLaunchKernelEx(&cfg, umma_step_kernel<1, 64, 2, 1>, A);

@@ -32,7 +32,8 @@ struct UmmaPlan {
     int bk = 64;             // k-block of the tcgen05 kernel (64 or 32)
     int order = 0;           // tile order (see umma_schedule)
     int mode = 0;            // 0 one CTA per 128x256 tile; 2 2-SM UMMA (cta_group::2) on
-                             // 256x256 tiles
+                             // 256x256 tiles; 3 the same with twelve epilogue warps and
+                             // four operand stages (instead of eight and five)
     int nacc = 2;            // accumulators per CTA in mode 2 (1 or 2)
     bool cubic = false;      // every step has c = 0 (BF16 only): B = b A comes from the
                              // Gram epilogue and there are no square tiles
@@ -40,6 +41,8 @@ struct UmmaPlan {
                              // (its own kernel instantiation; mode 0, 64-wide k-blocks)
     int max_clusters2 = 0;   // co-resident clusters of two, 2-SM kernel (0: unavailable)
     size_t smem_bytes2 = 0;  // dynamic shared memory of the 2-SM kernel
+    int max_clusters3 = 0;   // the same for the mode-3 kernel
+    size_t smem_bytes3 = 0;
     int* need2 = nullptr;    // device: per matrix readiness targets of 2-SM plans
     std::vector<TileTask> ph2_t[3];   // 256 x 256 tiles (2-SM plans)
     std::vector<double> ph2_c[3];

@@ -179,12 +179,13 @@ def _even(seed=31):
 @pytest.mark.parametrize("dtype", ["bf16"])
 def test_two_sm_mode_bitwise(dtype):
     """2-SM UMMA (256 x 256 tiles) against the 1-SM kernel on sizes that are
-    multiples of 256, with one and with two accumulators."""
+    multiples of 256, with one and with two accumulators, and with twelve
+    epilogue warps (mode 3: every third 32-column chunk per warp)."""
     mats = _even()
     tab = table(1e-3, 5)
     outs = []
     try:
-        for mode, nacc in ((0, 0), (2, 1), (2, 2)):
+        for mode, nacc in ((0, 0), (2, 1), (2, 2), (3, 0)):
             pe.pe_debug_set(7, mode)
             pe.pe_debug_set(8, nacc)
             pe.pe_release()
@@ -348,7 +349,7 @@ def test_kblock_and_order_variants_bitwise(dtype):
     outs = []
     try:
         for bk, order, mode in ((64, 0, 0), (32, 0, 0), (64, 1, 0), (32, 1, 0), (64, 2, 0), (64, 4, 0),
-                                (64, 3, 0), (64, 0, 2), (64, 1, 2), (64, 4, 2)):
+                                (64, 3, 0), (64, 0, 2), (64, 1, 2), (64, 4, 2), (64, 0, 3), (64, 4, 3)):
             pe.pe_debug_set(5, bk)
             pe.pe_debug_set(6, order)
             pe.pe_debug_set(7, mode)
