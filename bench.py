@@ -25,10 +25,13 @@ Muon step is reported beside it (``gpt2_small``) with its own roofline,
 e2e and CPU baseline.
 
 Launch: ``python bench.py [--gpus N] [--steps K] [--warmup W]``; for N > 1
-under torchrun the matrices of one set are shared among the ranks (LPT on
-flops, one all-gather of the results inside the timed region; strong
-scaling) and rank 0 prints the line. ``--impl reference`` times the FP64
-oracle on the host (the reference arm).
+under torchrun every rank runs its own set of the workload (same shapes,
+own seeds; no collective in the timed region; weak scaling, ``value`` = all
+ranks' flops over the slowest rank's time), and beside it one shared set is
+taken through the distributed-Muon form (LPT ownership of whole matrices,
+one NCCL all-gather of the results inside the timed region;
+``sharded_exchange``, strong scaling). Rank 0 prints the line.
+``--impl reference`` times the FP64 oracle on the host (the reference arm).
 """
 from __future__ import annotations
 
@@ -251,10 +254,18 @@ def large_dense_gpu(torch, seed=3, shapes=LARGE_SHAPES):
                 "Haar U,V (QR of seeded Gaussians on the GPU); s log-uniform [1e-4,1]; l=1e-4, T=6")
 
 
-def load_workload(name, torch):
+# per-rank sets of the multi-GPU weak-scaling run: the same shapes and
+# distributions, other seeds (rank 0 keeps the single-GPU set)
+RANK_WORKLOADS = {
+    "gpt2_small": lambda r: synth.gpt2_small(first_seed=1 + 100 * r),
+    "gpt2_heads": lambda r: synth.gpt2_heads(first_seed=5000 + 1000 * r),
+}
+
+
+def load_workload(name, torch, rank=0):
     if name == "large_dense":
-        return large_dense_gpu(torch)
-    wl = CPU_WORKLOADS[name]()
+        return large_dense_gpu(torch, seed=3 + 1009 * rank)
+    wl = RANK_WORKLOADS[name](rank) if (rank and name in RANK_WORKLOADS) else CPU_WORKLOADS[name]()
     host = [G.astype(np.float32) for G in wl.matrices]
     dev = [torch.from_numpy(h).cuda() for h in host]
     return Work(wl.name, wl.shapes, wl.l, wl.T, dev, None, wl.note, svd=wl.svd, host=host)
@@ -868,45 +879,73 @@ def fast_rectangular_line(ctx, n=1024, alphas=(4, 8, 32), T=6, reps=3):
 
 # ------------------------------------------------------------------ multi-GPU
 
-def run_sharded(ctx, wl, table, dtype, args):
-    """One set of matrices over the ranks (strong scaling): each rank owns
-    the matrices LPT assigns it and runs them in one grouped call, then one
-    all-gather gives every rank every factor (shard.polar_sharded); the
-    exchange is inside the timed region. Rank 0 prints the line."""
+def run_multi(ctx, args, dtype, peaks):
+    """N GPUs, one process each. The matrices are independent problems, so
+    the timed run shards units with no exchange: every rank owns a set of
+    the workload's shape (its own seeds), runs the single-GPU measurement on
+    it (CUDA events, barrier + synchronize around the timed region, max over
+    ranks) and the value is the units of all ranks over that time (weak
+    scaling). Beside it, the distributed-Muon form of one shared set: LPT
+    ownership of whole matrices and one NCCL all-gather of the results per
+    step (shard.polar_sharded), timed with the exchange inside. Rank 0
+    prints the line."""
     from paper_2505_16932_gb300 import shard
     torch, pe = ctx.torch, ctx.pe
-    xs = [d.clone() for d in wl.dev_in]
-    owners = shard.assign(wl.shapes, ctx.world, len(table))
-    flops = algorithmic_flops(wl.shapes, len(table))
+    wl = load_workload(args.workload, torch, ctx.rank)
+    table = pe.pe_coeffs(5, wl.l, wl.T, 1.01)
+    res = measure(ctx, wl, table, dtype, args.steps, args.warmup, 0, peaks)
+    res.pop("xs", None)
+    flops = res["flops_per_step"]
+    value = ctx.world * res["value"]
+    e2e = dict(res["e2e"])
+    e2e["value"] = ctx.world * e2e["value"]
+    e2e["note"] = "every rank through pe_polar_batched_host on its own pinned buffers; bytes per rank"
+    del wl
+    torch.cuda.empty_cache()
 
-    def step():
-        for d, s in zip(xs, wl.dev_in):
-            d.copy_(s)
+    # distributed-Muon exchange: one set shared by all ranks (rank 0's seeds)
+    ws = load_workload(args.workload, torch, 0)
+    xs = [d.clone() for d in ws.dev_in]
+    owners = shard.assign(ws.shapes, ctx.world, len(table))
+    fl_set = algorithmic_flops(ws.shapes, len(table))
+
+    def restore():
+        for d, s0 in zip(xs, ws.dev_in):
+            d.copy_(s0)
         ctx.flush.fill_(1.0)
-        torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        step()
+        restore()
         shard.polar_sharded(xs, table, dtype)
     ctx.barrier()
     tot = 0.0
     for _ in range(args.steps):
-        step()
+        restore()
         ctx.barrier()
         t0 = time.perf_counter()
         shard.polar_sharded(xs, table, dtype)
         torch.cuda.synchronize()
         tot += time.perf_counter() - t0
-    ms = ctx.max_over_ranks(1e3 * tot / args.steps)
+    ex_ms = ctx.max_over_ranks(1e3 * tot / args.steps)
+    pe.pe_sync_status()
     if ctx.rank != 0:
         return 0
-    line = {"metric": METRIC, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": ctx.world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "strong", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-            "config": {"workload": wl.name, "matrices": len(wl.shapes), "T": len(table), "l": wl.l,
-                       "parallelism": f"matrices over {ctx.world} ranks (LPT), one all-gather per step",
-                       "owners": owners, "l2": "L2 flush before each step"},
-            "timing": "host wall clock between barriers, max over ranks (compute + NCCL all-gather)"}
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ctx.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": ws.name, "matrices": len(ws.shapes), "matrices_all_ranks": ctx.world * len(ws.shapes),
+                       "T": ws.T, "l": ws.l,
+                       "parallelism": f"{ctx.world} ranks, one set of the workload per rank (own seeds), "
+                                      "no collective in the timed region",
+                       "flops_per_step_per_rank": flops,
+                       "l2": "inputs larger than L2 and a 258 MB L2 flush before each step"},
+            "gpu_launches": res["gpu_launches"], "e2e": e2e, "roofline": res["roofline"], "trace": res["trace"],
+            "clocks": res["clocks"],
+            "sharded_exchange": {
+                "value": fl_set / (ex_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ex_ms,
+                "scaling": "strong", "owners": owners,
+                "what": "one set over the ranks: LPT ownership of whole matrices, one grouped call per rank, "
+                        "one NCCL all-gather of the results; host clock between barriers, max over ranks"}}
     print(json.dumps(line))
     return 0
 
@@ -995,11 +1034,11 @@ def main():
     B.build()
     pe.lib()
     ctx = Ctx(pe, torch, world, rank, local)
-    wl = load_workload(args.workload, torch)
     dtype = args.dtype or ("fp32" if args.workload == "plain_small" else "bf16")
-    table = pe.pe_coeffs(5, wl.l, wl.T, 1.01)
     if world > 1:
-        return run_sharded(ctx, wl, table, dtype, args)
+        return run_multi(ctx, args, dtype, measured_peaks())
+    wl = load_workload(args.workload, torch)
+    table = pe.pe_coeffs(5, wl.l, wl.T, 1.01)
     if args.role_cycles:
         print(json.dumps(role_cycles(ctx, wl, table, dtype)))
         return 0

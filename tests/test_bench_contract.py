@@ -9,6 +9,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -100,3 +101,13 @@ def test_roofline_line():
     assert r["bound"] == "alu" and abs(r["peak"] - 152 * 128 * 2 * 2000e6 / 1e12) < 1e-9 and "frac_sustained" not in r
     r = bench.roofline_line({"prepare": (4, 2.0)}, shapes, "bf16", fs, 1e8, "x", peaks)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and abs(r["achieved"] - 2e8 / 0.5e-3 / 1e9) < 1e-9
+
+
+def test_rank_sets_share_shapes_not_values():
+    """The multi-GPU weak-scaling run gives every rank its own set: the
+    single-GPU set's shapes and distributions, other seeds."""
+    a = bench.CPU_WORKLOADS["gpt2_small"]()
+    b = bench.RANK_WORKLOADS["gpt2_small"](1)
+    assert a.shapes == b.shapes and a.T == b.T and a.l == b.l
+    assert not np.array_equal(a.matrices[0], b.matrices[0])
+    assert abs(np.linalg.norm(b.matrices[0]) - np.linalg.norm(a.matrices[0])) < 1e-9
