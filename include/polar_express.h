@@ -264,14 +264,6 @@ void pe_release(void);
  *          0 = default).
  *   key 9: value != 0 turns off the pairing of BF16 matrices with a short
  *          side <= 64 in plans built from now on (0 = pairing on).
- *   key 10: 1 runs the prepare (normalisation, cast, transpose) inside the
- *          first polynomial step's persistent launch, its strips taken by the
- *          epilogue warps between tiles, in BF16 plans built from now on
- *          (-1 or 0 = its own launch, the default); any other value is
- *          PE_EINVAL. Results are bitwise equal either way.
- *   key 11: with key 10, the strips of matrices up to this many ranks ahead
- *          of a Gram tile run before it (0 = default: the number of
- *          matrices / 8, at least 1).
  * Returns PE_EINVAL for an unknown key.
  */
 int pe_debug_set(int key, int64_t value);

@@ -37,8 +37,6 @@ int g_dbg_bk = 0;      // 0: default k-block
 int g_dbg_order = -1;  // -1: default tile order
 int g_dbg_mode = -1;   // -1: autotuned; 0 / 2: force the tcgen05 kernel mode
 int g_dbg_nacc = 0;    // 0: default accumulators of 2-SM plans; 1 or 2
-int g_dbg_fuse = -1;   // -1 / 0: prepare in its own launch; 1: inside the first step
-int64_t g_dbg_lag = 0; // prepare strips run this many matrix ranks ahead of the Gram tiles (0: default)
 bool g_dbg_nopair = false;   // true: no packing of small matrices in plans built from now on
 
 // tracing: (kind, start, stop) event triples recorded on the call's stream
@@ -403,11 +401,11 @@ int build_plan(const PlanKey& key, Plan** out) {
             o_fred[k] = cv.take(sizeof(FastReduce) * std::max<size_t>(1, fast_tasks), 64);
         }
     }
-    P->n_counters = 3 * count + 64;   // readiness (2 per matrix), spare, fused-prepare blocks (1 per matrix)
+    P->n_counters = 2 * count + 64;
     const size_t o_cnt = cv.take(sizeof(int) * P->n_counters, 64);
     size_t o_umma = 0, umma_bytes = 0;
     if (dtype != PE_FP32) {
-        umma_bytes = umma_workspace_bytes(P->mats.data(), count, (int)prep.size());
+        umma_bytes = umma_workspace_bytes(P->mats.data(), count);
         o_umma = cv.take(umma_bytes, 1024);
     }
     P->ws_bytes = cv.off;
@@ -554,17 +552,6 @@ int build_plan(const PlanKey& key, Plan** out) {
         }
         for (int t = 0; t < key.T && cubic; ++t) cubic = (key.coef[3 * t + 2] == 0.f);
         P->umma.cubic = cubic;
-        // the prepare may run inside the first step (BF16 without the fused
-        // Muon front end, not a long-side split)
-        P->umma.prep_ok = (dtype == PE_BF16) && key.w.empty() && !(key.flags & kFlagSplit) && key.restart == 0;
-        P->umma.fuse_prep = (g_dbg_fuse == 1) ? 1 : 0;
-        P->umma.prep_lag = (int)g_dbg_lag;
-        P->umma.prep_mat.clear();
-        for (const TileTask& t : prep) P->umma.prep_mat.push_back(t.mat);
-        P->umma.prep_list = P->d_prep;
-        P->umma.prep_partials = P->d_partials;
-        P->umma.prep_ticket = P->d_ticket;
-        P->umma.prep_done = P->d_counters + 2 * count + 64;
         int ust = umma_build(&P->umma, P->mats.data(), P->d_mats, count, dtype, P->ds->sms,
                              base + o_umma, umma_bytes, P->d_counters, tune, &g_err);
         if (ust != PE_OK) return ust;
@@ -650,18 +637,12 @@ int enqueue(Plan* P, cudaStream_t st, bool tuning = false) {
     if (!k.w.empty()) outputs |= kPrepMuon;                              // fused Muon step: momentum in prepare
     if (tuning) outputs |= kPrepNoMom;                                    // a tuning run leaves M unchanged
     outputs |= kPrepSkipPad;
-    // the prepare runs inside the first fused step when the schedule says so
-    const bool fuse_prep = k.dtype == PE_BF16 && P->umma.prep_ok && P->umma.fuse_prep &&
-                           !(k.flags & PE_BATCH_PHASED) && k.restart == 0;
-    if (fuse_prep) {
-        // readiness counters start at zero (the prepare kernel clears them otherwise)
-        PE_CU(cudaMemsetAsync(P->d_counters, 0, sizeof(int) * P->n_counters, st));
-    } else {
+    {
         TraceScope ts(1, st);
         PE_CU(launch_prepare(P->d_mats, (int)P->mats.size(), P->d_prep, P->n_prep, P->d_partials, k.scale, k.eps, outputs,
                              P->d_nscale, P->ds->status, P->d_counters, P->n_counters, P->d_ticket, st));
-        ++nk;
     }
+    ++nk;
     if (k.restart > 0) {
         const int r = enqueue_fast(P, st, &nk);
         if (r != PE_OK) return r;
@@ -694,9 +675,8 @@ int enqueue(Plan* P, cudaStream_t st, bool tuning = false) {
             P->umma.prof = g_dbg_prof;
             if (!phased) {
                 TraceScope ts(5, st);
-                const PrepFuse pf{outputs, k.scale, k.eps};
                 e = umma_step(&P->umma, t, a, b, c, last, -1, withhold, (uint64_t)g_dbg_wait_ns,
-                              P->ds->status, st, &n_launched, (fuse_prep && t == 0) ? &pf : nullptr);
+                              P->ds->status, st, &n_launched);
             } else {
                 for (int ph = 0; ph < 3 && e == cudaSuccess; ++ph) {
                     TraceScope ts(6 + ph, st);
@@ -722,7 +702,7 @@ int enqueue(Plan* P, cudaStream_t st, bool tuning = false) {
 // buffer is read by prepare but never written). Results are cached per
 // device and shape signature in memory and, when PE_AUTOTUNE_CACHE names a
 // file, in that file as JSON lines {"key": "...", "order": n} with
-// n = 256 * (prepare inside the first step) + 16 * kernel mode + tile order.
+// n = 16 * kernel mode + tile order.
 
 std::map<std::string, int> g_tune;
 bool g_tune_loaded = false;
@@ -777,19 +757,18 @@ int autotune(Plan* P, cudaStream_t st) {
     const std::string key = tune_key(P->key, P->ds);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-        const int fuse = it->second / 256, mode = (it->second / 16) % 16, order = it->second % 16;
+        const int mode = it->second / 16, order = it->second % 16;
         if ((mode != 0 && mode != 2 && mode != 3) || (mode == 2 && P->umma.max_clusters2 < 1) ||
-            (mode == 3 && P->umma.max_clusters3 < 1) || (fuse && !P->umma.prep_ok))
+            (mode == 3 && P->umma.max_clusters3 < 1))
             return PE_OK;   // cached on another configuration
         P->umma.mode = mode;
-        P->umma.fuse_prep = (g_dbg_fuse >= 0) ? g_dbg_fuse : fuse;
         return umma_schedule(&P->umma, order, &g_err);
     }
     cudaEvent_t a = nullptr, b = nullptr;
     PE_CU(cudaEventCreate(&a));
     PE_CU(cudaEventCreate(&b));
     PE_CU(cudaStreamSynchronize(st));
-    int best_order = P->umma.order, best_mode = P->umma.mode, best_fuse = P->umma.fuse_prep;
+    int best_order = P->umma.order, best_mode = P->umma.mode;
     int r = PE_OK;
     const int n_orders = (P->key.count >= 8) ? 5 : 2;   // lagged interleaves need several matrices
     std::vector<int> modes;
@@ -799,21 +778,14 @@ int autotune(Plan* P, cudaStream_t st) {
         if (P->umma.max_clusters2 > 0) modes.push_back(2);
         if (P->umma.max_clusters3 > 0) modes.push_back(3);
     }
-    // prepare in its own launch, or inside the first step (debug key 10; not
-    // a tuning candidate: the first step's epilogue warps keep a third of the
-    // prepare kernel's loads in flight, and the fused form measured slower on
-    // the GPT-2-small step and within noise on the large set)
-    std::vector<int> fuses{P->umma.prep_ok ? P->umma.fuse_prep : 0};
     // Round robin over the candidates (a warm-up pass, then two timed passes,
     // the faster run of each candidate counts), so that a drift of clocks or
     // power during tuning does not favour the candidates timed first.
-    const int per_fuse = n_orders * (int)modes.size();
-    const int ncand = per_fuse * (int)fuses.size();
+    const int ncand = n_orders * (int)modes.size();
     std::vector<float> cand_ms(ncand, 1e30f);
     for (int pass = 0; pass < 3 && r == PE_OK; ++pass) {
         for (int cand = 0; cand < ncand && r == PE_OK; ++cand) {
-            P->umma.fuse_prep = fuses[cand / per_fuse];
-            P->umma.mode = modes[(cand % per_fuse) / n_orders];
+            P->umma.mode = modes[cand / n_orders];
             r = umma_schedule(&P->umma, cand % n_orders, &g_err);
             if (r != PE_OK) break;
             cudaEventRecord(a, st);
@@ -829,16 +801,14 @@ int autotune(Plan* P, cudaStream_t st) {
         int bc = 0;
         for (int cand = 1; cand < ncand; ++cand)
             if (cand_ms[cand] < cand_ms[bc]) bc = cand;
-        best_fuse = fuses[bc / per_fuse];
-        best_mode = modes[(bc % per_fuse) / n_orders];
+        best_mode = modes[bc / n_orders];
         best_order = bc % n_orders;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (r != PE_OK) return r;
-    tune_store(key, 256 * best_fuse + 16 * best_mode + best_order);
+    tune_store(key, 16 * best_mode + best_order);
     P->umma.mode = best_mode;
-    P->umma.fuse_prep = best_fuse;
     return umma_schedule(&P->umma, best_order, &g_err);
 }
 
@@ -1447,11 +1417,6 @@ int pe_debug_set(int key, int64_t value) {
             return PE_OK;
         case 8: pe::g_dbg_nacc = (int)value; return PE_OK;
         case 9: pe::g_dbg_nopair = value != 0; return PE_OK;
-        case 10:
-            if (value != -1 && value != 0 && value != 1) return pe::fail(PE_EINVAL, "prepare fusion must be -1, 0 or 1");
-            pe::g_dbg_fuse = (int)value;
-            return PE_OK;
-        case 11: pe::g_dbg_lag = value < 0 ? 0 : value; return PE_OK;
         default: return pe::fail(PE_EINVAL, "unknown debug key");
     }
 }

@@ -49,7 +49,6 @@
 #include <vector>
 
 #include "pe_internal.h"
-#include "pe_prep_body.cuh"
 #include "pe_umma.h"
 
 namespace pe {
@@ -92,17 +91,6 @@ struct StepArgs {
     uint64_t wait_ns;
     long long* prof;    // optional per-CTA cycle counters (debug)
     const float* nscale;  // per-matrix normalisation factor, applied in step 0
-    // Prepare fused into the first step (prep_done != null): kPrep entries of
-    // the tile list name prepare strips (TileTask::tm for the CTA of rank 0,
-    // tn for rank 1; -1 none), which the first eight epilogue warps run; the
-    // last strip of each 64-row block adds one to prep_done[descriptor], and
-    // every tile of the launch waits until its descriptor is complete.
-    int* prep_done;
-    const TileTask* prep_tiles;
-    double* prep_partials;
-    unsigned* prep_ticket;
-    float prep_scale, prep_eps;
-    int prep_outputs;
 };
 
 // ------------------------------------------------------------- PTX helpers
@@ -326,7 +314,6 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 template <int N>
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory"); }
 
-
 // Bounded wait for a readiness counter (fused mode). On expiry the status
 // word records a timeout and the caller proceeds: the launch always ends,
 // with invalid results that pe_sync_status reports.
@@ -381,13 +368,8 @@ __device__ __forceinline__ float d_of(float ta, const StepArgs& A, const DevMat&
 
 // ------------------------------------------------------------ tile geometry
 
-// TileTask::kind carries the product in its low bits; kind kPrep (3) is a
-// prepare entry of a first step with the prepare fused in.
+// TileTask::kind carries the product in its low bits.
 constexpr int kKindMask = 3;
-constexpr int kPrep = 3;
-
-// 64-row blocks of a descriptor whose prepare must finish before its tiles run
-__device__ __forceinline__ int prep_target(const DevMat& M) { return M.npack ? kMaxPack : 1; }
 
 struct Geo {
     int kind, mat, tm, tn, bn, nkb;
@@ -734,9 +716,6 @@ __global__ void __launch_bounds__(threads_of(EW), 1) umma_step_kernel(const __gr
     uint64_t* dfull = reinterpret_cast<uint64_t*>(tmem_slot + 2);   // d ring: slot written
     uint64_t* dempty = dfull + kDRing;                              // d ring: slot read by every epilogue warp
     float* dring = reinterpret_cast<float*>(dempty + kDRing);       // kDRing x 4 (a value per 64-row block)
-    // barrier of the 256 threads of the first eight epilogue warps (fused
-    // prepare strips): an mbarrier, so that every wait on it is bounded
-    uint64_t* prepbar = reinterpret_cast<uint64_t*>(dring + 4 * kDRing);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t limit = A.wait_ns ? A.wait_ns : kDefaultWaitNs;
@@ -764,7 +743,6 @@ __global__ void __launch_bounds__(threads_of(EW), 1) umma_step_kernel(const __gr
             mbar_init(&dfull[k], 1);
             mbar_init(&dempty[k], kEpiWarps);
         }
-        mbar_init(prepbar, 256);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
@@ -807,16 +785,9 @@ __global__ void __launch_bounds__(threads_of(EW), 1) umma_step_kernel(const __gr
         long long c_dep = 0, c_empty = 0;
         for (int it = t_begin; it < t_end && ok; ++it) {
             const TileTask tk = PE_TILE(it);
-            if (NS == 1 && !GF32 && tk.kind == kPrep) continue;
             const DevMat& M = A.mats[tk.mat];
             const Geo g = tile_geo<BK>(tk, M, A.cur);
             const CUtensorMap* mp = A.maps + (size_t)tk.mat * kMapsPerMat;
-            if (NS == 1 && !GF32 && A.prep_done) {   // X of this descriptor comes from the fused prepare
-                const long long c0 = clock64();
-                wait_counter(A.prep_done + tk.mat, prep_target(M), limit, A.status);
-                fence_proxy_async_global();
-                c_dep += clock64() - c0;
-            }
             if (A.dependent && g.kind != kGram) {
                 const long long c0 = clock64();
                 const int which = (g.kind == kSquare || A.cubic) ? 0 : 1;   // wait for A, or for B
@@ -899,7 +870,6 @@ __global__ void __launch_bounds__(threads_of(EW), 1) umma_step_kernel(const __gr
         long long c_full = 0, c_tempty = 0;
         for (int it = t_begin; it < t_end && ok; ++it) {
             const TileTask tk = PE_TILE(it);
-            if (tk.kind == kPrep) continue;
             const DevMat& M = A.mats[tk.mat];
             const Geo g = tile_geo<BK>(tk, M, A.cur);
             long long c0 = clock64();
@@ -964,7 +934,6 @@ __global__ void __launch_bounds__(threads_of(EW), 1) umma_step_kernel(const __gr
             uint32_t ph = 0;
             for (int it = t_begin; it < t_end; ++it) {
                 const TileTask tk = PE_TILE(it);
-                if (tk.kind == kPrep) continue;
                 const DevMat& M = A.mats[tk.mat];
                 if ((tk.kind & kKindMask) == kGram || !M.btr || A.cubic) continue;
                 if (!mbar_wait(&dempty[slot], ph ^ 1, limit, abort_flag)) {
@@ -1017,57 +986,13 @@ __global__ void __launch_bounds__(threads_of(EW), 1) umma_step_kernel(const __gr
         uint32_t acc_phase = 0;
         int dslot = 0;         // d ring slot of the next square / update tile
         uint32_t dph = 0;
-        uint32_t prep_ph = 0;  // phase of the fused prepare's barrier
         long long c_tfull = 0, c_dep = 0, c_gram = 0, c_sq = 0, c_ap = 0, c_rdx = 0, c_pf = 0, c_math = 0, c_st = 0, c_fn = 0,
                   c_is = 0, c_tm = 0;
         for (int it = t_begin; it < t_end; ++it) {
             const TileTask tk = PE_TILE(it);
-            if constexpr (NS == 1 && !GF32) {
-                if (tk.kind == kPrep) {
-                    // a prepare strip of the fused first step, run by the first
-                    // eight epilogue warps with the shared tile in the staging
-                    // of warps 0-2 (free once every warp's stores have read
-                    // their boxes; all operand prefetches were consumed)
-                    if (ew < 8) {
-                        // a wait that gives up latches the abort (status bit 4); the
-                        // strip then runs on without it and the launch still ends
-                        auto sync = [&] {
-                            mbar_arrive(prepbar);
-                            if (!mbar_wait(prepbar, prep_ph, limit, abort_flag)) {
-                                *abort_flag = 1;
-                                atomicOr(A.status, 4);
-                            }
-                            prep_ph ^= 1;
-                        };
-                        if (lane == 0) bulk_wait_read0();
-                        __syncwarp();
-                        sync();
-                        const int idx = crank ? tk.tn : tk.tm;
-                        if (idx >= 0) {
-                            uint8_t* pb = smem + C::kEpiOff;
-                            prep::strip<false>(A.mats, A.nmats, A.prep_tiles, idx, A.prep_partials, A.prep_scale,
-                                               A.prep_eps, A.prep_outputs, const_cast<float*>(A.nscale), A.status,
-                                               A.prep_ticket, A.prep_done, etid, reinterpret_cast<float(*)[65]>(pb),
-                                               reinterpret_cast<double*>(pb + 64 * 65 * 4),
-                                               reinterpret_cast<int*>(pb + 64 * 65 * 4 + 8 * 8), sync);
-                        }
-                        // the tile's generic accesses before later TMA copies into the staging
-                        fence_async_smem();
-                        sync();
-                    }
-                    continue;
-                }
-            }
             const DevMat& M = A.mats[tk.mat];
             const Geo g = tile_geo<BK>(tk, M, A.cur);
             const CUtensorMap* mp = A.maps + (size_t)tk.mat * kMapsPerMat;
-            if (NS == 1 && !GF32 && A.prep_done) {   // X and its normalisation factor come from the fused prepare
-                if (lane == 0) {
-                    wait_counter(A.prep_done + tk.mat, prep_target(M), limit, A.status);
-                    fence_proxy_async_global();
-                }
-                __syncwarp();
-            }
             // the warp's first row (2-SM: this CTA holds rows 128 crank .. of the 256-row tile)
             const int gi0 = (kCg2 ? tk.tm * 2 * kBM + crank * kBM : g.tm * kBM) + q * 32;
             const int gi = gi0 + lane;
@@ -1080,7 +1005,7 @@ __global__ void __launch_bounds__(threads_of(EW), 1) umma_step_kernel(const __gr
             // step 0 runs on the unscaled prepared X and applies the
             // normalisation factor s: A = s^2 X X^T, X_1 = s (a X + B X)
             // (a warp's 32 rows lie in one 64-row block of a pack)
-            const float s0 = (A.step == 0) ? __ldcg(A.nscale + (M.npack ? (gi0 >> 6) : 0) * A.nmats + g.mat) : 1.f;
+            const float s0 = (A.step == 0) ? A.nscale[(M.npack ? (gi0 >> 6) : 0) * A.nmats + g.mat] : 1.f;
             if (g.kind == kSquare && A.dependent) {   // A (FP32) comes from other CTAs
                 const long long c0 = clock64();
                 if (NS == 1) {
@@ -1524,61 +1449,6 @@ void lpt_units(const std::vector<Unit>& order, int groups, std::vector<int>* off
     (*off)[groups] = n;
 }
 
-// The first step's lists with the prepare fused in. Matrices are ranked by
-// the first appearance of their Gram tiles in the fused order; the strips go
-// round robin, in rank order, to the CTAs (both CTAs of a 2-SM unit get their
-// own strip in one entry), and each unit runs its strips of the matrices up
-// to `lag` ranks ahead of a Gram tile before that tile, the rest before its
-// first square or update tile.
-void first_step_list(const UmmaPlan* P, const std::vector<Unit>& fused, int groups, bool cg2,
-                     const std::vector<int>& off, const std::vector<TileTask>& list, std::vector<int>* off0,
-                     std::vector<TileTask>* list0) {
-    const int count = P->count;
-    std::vector<int> rank(count, -1);
-    int nr = 0;
-    for (const Unit& u : fused)
-        if ((u.t.kind & kKindMask) == kGram && rank[u.t.mat] < 0) rank[u.t.mat] = nr++;
-    for (int m = 0; m < count; ++m)
-        if (rank[m] < 0) rank[m] = nr++;
-    const int lag = P->prep_lag > 0 ? P->prep_lag : std::max(1, count / 8);
-    const int ns = (int)P->prep_mat.size();
-    std::vector<int> strips(ns);
-    for (int i = 0; i < ns; ++i) strips[i] = i;
-    std::stable_sort(strips.begin(), strips.end(),
-                     [&](int a, int b) { return rank[P->prep_mat[a]] < rank[P->prep_mat[b]]; });
-    const int slots = cg2 ? 2 * groups : groups;
-    std::vector<std::vector<int>> per(slots);
-    for (int k = 0; k < ns; ++k) per[k % slots].push_back(strips[k]);
-    off0->assign(groups + 1, 0);
-    list0->clear();
-    for (int u = 0; u < groups; ++u) {
-        (*off0)[u] = (int)list0->size();
-        const std::vector<int>& s0 = per[cg2 ? 2 * u : u];
-        const std::vector<int>* s1 = cg2 ? &per[2 * u + 1] : nullptr;
-        const size_t ne = std::max(s0.size(), s1 ? s1->size() : (size_t)0);
-        size_t e = 0;
-        auto emit_upto = [&](int r) {   // entries whose strips belong to matrices of rank <= r
-            while (e < ne) {
-                const int a = e < s0.size() ? s0[e] : -1;
-                const int b = (s1 && e < s1->size()) ? (*s1)[e] : -1;
-                const int ra = a >= 0 ? rank[P->prep_mat[a]] : nr;
-                const int rb = b >= 0 ? rank[P->prep_mat[b]] : nr;
-                if (std::min(ra, rb) > r) break;
-                list0->push_back(TileTask{P->prep_mat[a >= 0 ? a : b], a, b, kPrep});
-                ++e;
-            }
-        };
-        for (int i = off[u]; i < off[u + 1]; ++i) {
-            const TileTask& t = list[i];
-            if ((t.kind & kKindMask) == kGram) emit_upto(rank[t.mat] + lag);
-            else emit_upto(nr);
-            list0->push_back(t);
-        }
-        emit_upto(nr);
-    }
-    (*off0)[groups] = (int)list0->size();
-}
-
 }  // namespace
 
 int umma_schedule(UmmaPlan* P, int order, std::string* err) {
@@ -1621,14 +1491,6 @@ int umma_schedule(UmmaPlan* P, int order, std::string* err) {
     lpt_units(fused, groups, &off, &list);
     cudaError_t e = cudaMemcpy(P->tiles, list.data(), sizeof(TileTask) * list.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->tile_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && P->prep_ok && P->fuse_prep) {
-        std::vector<int> off0;
-        std::vector<TileTask> list0;
-        first_step_list(P, fused, groups, cg2, off, list, &off0, &list0);
-        e = cudaMemcpy(P->tiles0, list0.data(), sizeof(TileTask) * list0.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(P->tile_off0, off0.data(), sizeof(int) * off0.size(), cudaMemcpyHostToDevice);
-    }
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
         std::vector<int> poff;
         std::vector<TileTask> plist;
@@ -1647,7 +1509,7 @@ int umma_schedule(UmmaPlan* P, int order, std::string* err) {
     return PE_OK;
 }
 
-size_t umma_workspace_bytes(const DevMat* mats, int count, int n_prep) {
+size_t umma_workspace_bytes(const DevMat* mats, int count) {
     size_t tiles = 0;
     for (int i = 0; i < count; ++i) {
         const size_t tm = mats[i].sp / kBM;
@@ -1658,8 +1520,6 @@ size_t umma_workspace_bytes(const DevMat* mats, int count, int n_prep) {
     size_t b = 0;
     b += align_up(sizeof(CUtensorMap) * kMapsPerMat * count, 1024);
     b += 2 * align_up(sizeof(TileTask) * (tiles + 2), 256);   // fused + phased lists
-    b += align_up(sizeof(TileTask) * (tiles + n_prep + 2), 256);   // first step with the prepare
-    b += align_up(sizeof(int) * (4096 + 1), 256);
     b += 4 * align_up(sizeof(int) * (4096 + 1), 256);         // CSR offsets (grid <= 4096)
     b += 2 * align_up(sizeof(int) * 2 * count, 256);
     return b + 4096;
@@ -1758,8 +1618,6 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
     P->need = reinterpret_cast<int*>(take(sizeof(int) * 2 * count, 256));
     P->need2 = reinterpret_cast<int*>(take(sizeof(int) * 2 * count, 256));
     TileTask* ph_base = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (ntot + 2), 256));
-    P->tiles0 = reinterpret_cast<TileTask*>(take(sizeof(TileTask) * (ntot + P->prep_mat.size() + 2), 256));
-    P->tile_off0 = reinterpret_cast<int*>(take(sizeof(int) * (sms + 1), 256));
     size_t ph_pos = 0;
     for (int k = 0; k < 3; ++k) {
         P->ph_tiles[k] = ph_base + ph_pos;
@@ -1871,9 +1729,8 @@ int umma_build(UmmaPlan* P, DevMat* mats, DevMat* d_mats, int count, int dtype, 
 }
 
 cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, int phase, int withhold,
-                      uint64_t wait_ns, int* status, cudaStream_t st, int* launched, const PrepFuse* prep) {
+                      uint64_t wait_ns, int* status, cudaStream_t st, int* launched) {
     StepArgs A;
-    memset(&A, 0, sizeof(A));
     A.nscale = P->nscale;
     A.mats = P->d_mats;
     A.maps = reinterpret_cast<const CUtensorMap*>(P->maps);
@@ -1931,17 +1788,6 @@ cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, i
         A.off = P->tile_off;
         A.tiles = P->tiles;
         A.dependent = 1;
-        if (prep && t == 0 && P->fuse_prep && P->prep_ok && P->nsplit == 1 && !P->gram_f32) {
-            A.off = P->tile_off0;
-            A.tiles = P->tiles0;
-            A.prep_done = P->prep_done;
-            A.prep_tiles = P->prep_list;
-            A.prep_partials = P->prep_partials;
-            A.prep_ticket = P->prep_ticket;
-            A.prep_scale = prep->scale;
-            A.prep_eps = prep->eps;
-            A.prep_outputs = prep->outputs;
-        }
         return go(P->grid, true);
     }
     A.dependent = 0;

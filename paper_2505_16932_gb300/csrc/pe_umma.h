@@ -53,21 +53,9 @@ struct UmmaPlan {
     std::vector<TileTask> ph_t[3];
     std::vector<double> ph_c[3];
     std::vector<double> mat_cost;
-    // prepare fused into the first step (BF16 path; see StepArgs::prep_done)
-    bool prep_ok = false;        // the plan may fuse it (set before umma_build)
-    int fuse_prep = 0;           // the schedule in use fuses it
-    int prep_lag = 0;            // strips of matrices up to this many ranks ahead of a
-                                 // Gram tile run before it (0: default)
-    std::vector<int> prep_mat;   // host: descriptor of each prepare strip, in list order
-    const TileTask* prep_list = nullptr;   // device: the plan's prepare strips
-    double* prep_partials = nullptr;
-    unsigned* prep_ticket = nullptr;
-    int* prep_done = nullptr;    // device: finished 64-row blocks per descriptor
-    TileTask* tiles0 = nullptr;  // device: first-step list with the prepare entries
-    int* tile_off0 = nullptr;
 };
 
-size_t umma_workspace_bytes(const DevMat* mats, int count, int n_prep);
+size_t umma_workspace_bytes(const DevMat* mats, int count);
 
 // Builds tensor maps and schedules inside `ws` (device memory of
 // umma_workspace_bytes()); sets DevMat::out_tma and re-uploads the
@@ -82,11 +70,7 @@ int umma_schedule(UmmaPlan* P, int order, std::string* err);
 // Enqueue polynomial step t (0-based). phase < 0: one persistent launch of
 // the whole step with per-matrix readiness waits; phase 0/1/2: one grouped
 // launch of that product only (Gram, square, update).
-// With `prep` (first step, fused schedule), the launch also runs the prepare
-// strips (outputs, scale, eps as for launch_prepare).
-struct PrepFuse { int outputs; float scale, eps; };
 cudaError_t umma_step(UmmaPlan* P, int t, float a, float b, float c, int last, int phase,
-                      int withhold, uint64_t wait_ns, int* status, cudaStream_t st, int* launched,
-                      const PrepFuse* prep = nullptr);
+                      int withhold, uint64_t wait_ns, int* status, cudaStream_t st, int* launched);
 
 }  // namespace pe

@@ -467,67 +467,3 @@ def test_small_matrix_packs_bitwise_equal_unpacked():
     for X, G in zip(outs[0], mats):
         ref = O.polar_express(G.astype(np.float32).astype(np.float64), tab)
         assert O.rel_fro(X.numpy().astype(np.float64), ref) <= BF16_TOL
-
-
-# ------------------------------------------- prepare fused into the first step
-
-@pytest.mark.parametrize("mode", [0, 2, 3])
-def test_fused_prepare_bitwise(mode):
-    """The prepare strips run by the first step's epilogue warps (debug key
-    10) write the same X and normalisation factors as the prepare kernel, so
-    the result equals the unfused plan's bit for bit, for every lag of the
-    strips ahead of the Gram tiles: uneven shapes in both orientations and
-    small packed matrices (every padded size a multiple of 256, so that the
-    2-SM modes are offered)."""
-    shapes = ([(768, 2304), (3072, 768), (512, 512), (256, 1024)] + [(768, 64)] * 3 + [(40, 500)] * 2
-              + [(130, 700), (700, 130)])
-    mats = [synth.random_svd_case(seed=71 + i, m=m, n=n, lo=1e-3).G for i, (m, n) in enumerate(shapes)]
-    tab = table(1e-3, 4)
-    outs = []
-    try:
-        pe.pe_debug_set(7, mode)
-        for fuse, lag in ((0, 0), (1, 1), (1, 4), (1, 1000)):
-            pe.pe_debug_set(10, fuse)
-            pe.pe_debug_set(11, lag)
-            pe.pe_release()
-            for _ in range(2):   # the second call replays the captured graph
-                Xs = [to_dev(G) for G in mats]
-                pe.pe_polar_batched(Xs, tab, "bf16")
-            pe.pe_sync_status()
-            outs.append([X.cpu() for X in Xs])
-    finally:
-        pe.pe_debug_set(7, -1)
-        pe.pe_debug_set(10, -1)
-        pe.pe_debug_set(11, 0)
-        pe.pe_release()
-    for o in outs[1:]:
-        for a, b, sh in zip(outs[0], o, shapes):
-            assert torch.equal(a, b), sh
-    for X, G in zip(outs[0], mats):
-        ref = O.polar_express(G.astype(np.float32).astype(np.float64), tab)
-        assert O.rel_fro(X.numpy().astype(np.float64), ref) <= BF16_TOL
-
-
-def test_fused_prepare_bf16_io_and_host_entry():
-    """Fused prepare with BF16 caller buffers and through the host-buffer
-    entry (its per-group plans) equals the unfused path bit for bit."""
-    rng = np.random.default_rng(5)
-    mats = [rng.standard_normal(s) for s in ((512, 1536), (1536, 512), (300, 900))]
-    tab = table(1e-3, 3)
-    outs = []
-    try:
-        for fuse in (0, 1):
-            pe.pe_debug_set(10, fuse)
-            pe.pe_release()
-            Xs = [to_dev(G, torch.bfloat16) for G in mats]
-            pe.pe_polar_batched(Xs, tab, "bf16")
-            hin = [torch.from_numpy(G.astype(np.float32)) for G in mats]
-            hout = [torch.empty_like(h) for h in hin]
-            pe.pe_polar_batched_host(hin, hout, tab, "bf16")
-            pe.pe_sync_status()
-            outs.append([X.cpu() for X in Xs] + hout)
-    finally:
-        pe.pe_debug_set(10, -1)
-        pe.pe_release()
-    for a, b in zip(outs[0], outs[1]):
-        assert torch.equal(a, b)
