@@ -16,7 +16,8 @@
 //   fast_reduce_kernel    sums in chunk order before the same epilogue;
 //   fast_shift_kernel     Y += shift I on the first s diagonal entries.
 // FP32 FMA accumulation (no TF32), 8 x 8 outputs per thread, double-buffered
-// shared memory; every operand is zero-padded to whole tiles.
+// shared memory with rows padded by four floats, two blocks per SM; every
+// operand is zero-padded to whole tiles.
 #include <cuda_runtime.h>
 
 #include "pe_internal.h"
@@ -24,7 +25,7 @@
 namespace pe {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 16;
+constexpr int BM = 128, BN = 128, BK = 16, PAD = 4;
 
 // A: rows of op(A) K-contiguous (TA = false: a[i * lda + k]) or K rows of
 // op(A)'s columns (TA = true: a[k * lda + i]); B: K rows (b[k * ldb + j])
@@ -47,7 +48,7 @@ __device__ __forceinline__ void load_ab(const GemmTask& t, int r0, int c0, int k
 }
 
 template <bool TA>
-__device__ __forceinline__ void store_ab(float (*As)[BM], float (*Bs)[BN], int tid, const float4 (&ra)[2],
+__device__ __forceinline__ void store_ab(float (*As)[BM + PAD], float (*Bs)[BN + PAD], int tid, const float4 (&ra)[2],
                                          const float4 (&rb)[2]) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -68,10 +69,10 @@ __device__ __forceinline__ void store_ab(float (*As)[BM], float (*Bs)[BN], int t
 }
 
 template <bool TA>
-__global__ void __launch_bounds__(256) fast_gemm_kernel(const GemmTask* __restrict__ tasks, float alpha,
-                                                        float beta, float gamma) {
-    __shared__ __align__(16) float As[2][BK][BM];
-    __shared__ __align__(16) float Bs[2][BK][BN];
+__global__ void __launch_bounds__(256, 2) fast_gemm_kernel(const GemmTask* __restrict__ tasks, float alpha,
+                                                           float beta, float gamma) {
+    __shared__ __align__(16) float As[2][BK][BM + PAD];
+    __shared__ __align__(16) float Bs[2][BK][BN + PAD];
     const GemmTask t = tasks[blockIdx.x];
     const int r0 = t.tm * BM, c0 = t.tn * BN;
     const int tid = threadIdx.x;

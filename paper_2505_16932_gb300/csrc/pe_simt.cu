@@ -16,7 +16,9 @@
 // 128 x 128 output tile per block, BK = 16, 256 threads, 8 x 8 outputs per
 // thread as two 4 x 4 quadrants (rows ty*4 and 64 + ty*4, same for columns),
 // double-buffered shared memory filled from registers prefetched one k-tile
-// ahead. All operands are zero-padded to whole tiles, so there are no edge
+// ahead; two blocks per SM (128 registers). Shared rows are padded by four
+// floats, which keeps them 16-byte aligned for the vector reads and cuts the
+// bank conflicts of the transposing stores from four-way to two-way. All operands are zero-padded to whole tiles, so there are no edge
 // cases inside the product.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -26,7 +28,7 @@
 namespace pe {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 16;
+constexpr int BM = 128, BN = 128, BK = 16, PAD = 4;
 
 struct Operands {
     const float* a;   // rows of the left operand, K contiguous
@@ -54,7 +56,7 @@ __device__ __forceinline__ void load_tiles(const Operands& op, int r0, int c0, i
 }
 
 template <bool kBKMajor>
-__device__ __forceinline__ void store_tiles(float (*As)[BM], float (*Bs)[BN], int tid,
+__device__ __forceinline__ void store_tiles(float (*As)[BM + PAD], float (*Bs)[BN + PAD], int tid,
                                             const float4 (&ra)[2], const float4 (&rb)[2]) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -77,13 +79,13 @@ __device__ __forceinline__ void store_tiles(float (*As)[BM], float (*Bs)[BN], in
 }
 
 template <int kKind>
-__global__ void __launch_bounds__(256) simt_phase_kernel(const DevMat* __restrict__ mats,
+__global__ void __launch_bounds__(256, 2) simt_phase_kernel(const DevMat* __restrict__ mats,
                                                          const TileTask* __restrict__ tiles,
                                                          float ca, float cb, float cc, int src,
                                                          int last, int first, const float* __restrict__ nscale) {
     constexpr bool kBK = (kKind != kApply);
-    __shared__ __align__(16) float As[2][BK][BM];
-    __shared__ __align__(16) float Bs[2][BK][BN];
+    __shared__ __align__(16) float As[2][BK][BM + PAD];
+    __shared__ __align__(16) float Bs[2][BK][BN + PAD];
     const TileTask tk = tiles[blockIdx.x];
     const DevMat& M = mats[tk.mat];
     const int r0 = tk.tm * BM, c0 = tk.tn * BN;
