@@ -254,6 +254,29 @@ def test_batched_vs_oracle_uneven():
             assert O.rel_fro(X.cpu().numpy().astype(np.float64), ref) <= tol, (dtype, G.shape)
 
 
+# ------------------------------------------------------ degenerate inputs
+
+@pytest.mark.parametrize("dtype,tol", [("fp32", FP32_TOL), ("bf16", BF16_TOL), ("bf16x3", BF16_TOL)])
+def test_degenerate_inputs(dtype, tol):
+    """Inputs the method degenerates on. G = 0: the normalisation divides by
+    eps alone and X stays exactly zero through every step. A 1 x 1 matrix
+    (polar(g) = sign(g)), a single row and a single column (one singular
+    value each) and orthogonal rows (polar(Q) = Q, every normalised singular
+    value 1 / (1.01 sqrt(s))): each against the FP64 iteration at the
+    path's bar, and the 1 x 1 result with the sign of g."""
+    rng = np.random.default_rng(13)
+    tab = table(1e-3, 6)
+    Z = np.zeros((64, 200))
+    assert np.array_equal(run_single(Z, tab, dtype), Z)
+    Q, _ = np.linalg.qr(rng.standard_normal((640, 256)))
+    cases = [np.array([[-3.0]]), rng.standard_normal((1, 7)), rng.standard_normal((5, 1)), Q.T]
+    for G in cases:
+        ref = O.polar_express(G.astype(np.float32).astype(np.float64), tab)
+        got = run_single(G, tab, dtype)
+        assert O.rel_fro(got, ref) <= tol, (dtype, G.shape)
+    assert run_single(np.array([[-3.0]]), tab, dtype)[0, 0] < -0.9
+
+
 # ---------------------------------------------------- status / failures
 
 def test_nonfinite_input_reports_status():
