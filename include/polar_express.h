@@ -200,7 +200,7 @@ int pe_sync_status(void* stream);
  * copies run asynchronously at full link bandwidth. The library keeps device
  * staging buffers per shape set (4 sets, LRU; pe_release frees them) and
  * pipelines: the matrices are cut into `ngroups` contiguous groups of about
- * equal bytes (0 = automatic: min(count, 4)); group
+ * equal bytes (0 = automatic: min(count, 6)); group
  * g's host->device copies run on one internal stream, its grouped compute on
  * `stream` once they have landed, its device->host copies on a second
  * internal stream, so copies in both directions overlap compute of other

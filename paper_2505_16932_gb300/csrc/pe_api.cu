@@ -1028,7 +1028,7 @@ int run_host(const void* const* Hin, void* const* Hout, const int64_t* m, const 
         dims[2 * i + 1] = n[i];
         total += (size_t)(m[i] * n[i]);
     }
-    const int ng = std::min(count, ngroups > 0 ? ngroups : 4);
+    const int ng = std::min(count, ngroups > 0 ? ngroups : 6);
     // contiguous groups balanced by bytes
     std::vector<int> cut(ng + 1, count);
     cut[0] = 0;
