@@ -11,6 +11,8 @@
   composition p(x_i) of the oracle's table.
 * Uneven batch with spikes (96 + 16 matrices, T = 5): every matrix against
   the dense FP64 iteration.
+* Per-head splitting (576 head slices of 768 x 64 + 24 MLP matrices): every
+  element of every matrix against the FP64 iteration in spectral form.
 * Ill-conditioned spectra (2048^2, 4096 x 1024; l = 1e-7, T = 12): BF16x3 is
   closer to the FP64 iteration than BF16, on the restricted directions.
 * Newton-Schulz quintic through the same kernels; the longest supported
@@ -208,24 +210,20 @@ def test_longest_vector(path, tol):
     assert O.rel_fro(X.cpu().numpy().astype(np.float64), ref) <= tol
 
 
-def test_gpt2_per_head_batch_sampled():
-    """Per-head splitting (600 matrices: 576 head slices of 768 x 64 and the 24
-    MLP matrices) in one grouped call: one matrix of each shape against the
-    FP64 iteration in spectral form on 10^4 sampled entries."""
+def test_gpt2_per_head_batch_every_element():
+    """Per-head splitting (600 matrices: 576 head slices of 768 x 64, packed
+    four to a descriptor, and the 24 MLP matrices) in one grouped call: every
+    element of every matrix against the FP64 iteration in spectral form, at
+    the BF16 bar of 2e-2 relative Frobenius per matrix."""
     wl = synth.gpt2_heads()
     tab = pe.pe_coeffs(5, wl.l, wl.T, 1.01)
     Xs = [dev(G) for G in wl.matrices]
     pe.pe_polar_batched(Xs, tab, "bf16")
     pe.pe_sync_status()
-    rng = np.random.default_rng(2)
-    seen = set()
+    worst = 0.0
     for i, (X, sv, (m, n)) in enumerate(zip(Xs, wl.svd, wl.shapes)):
-        if (m, n) in seen and i not in (100, 377):
-            continue
-        seen.add((m, n))
-        r = rng.integers(0, m, 10000)
-        c = rng.integers(0, n, 10000)
-        ref = O.polar_express_spectral(sv.U, sv.s, sv.V, tab, rows=r, cols=c)
-        got = X[torch.from_numpy(r).cuda(), torch.from_numpy(c).cuda()].cpu().numpy().astype(np.float64)
-        rel = np.sqrt(np.mean((got - ref) ** 2) / np.mean(ref ** 2))
+        ref = O.polar_express_spectral(sv.U, sv.s, sv.V, tab)
+        rel = O.rel_fro(X.cpu().numpy().astype(np.float64), ref)
         assert rel <= 2e-2, ((m, n), i, rel)
+        worst = max(worst, rel)
+    assert worst > 0.0
