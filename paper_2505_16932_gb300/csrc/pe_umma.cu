@@ -688,6 +688,7 @@ enum ProfSlot {
 template <int NS, int BK, int MODE, int NACC, bool GF32 = false, int EW = 8>
 __global__ void __launch_bounds__(threads_of(EW), 1) umma_step_kernel(const __grid_constant__ StepArgs A) {
     using C = Cfg<NS, BK, MODE, EW>;
+    static_assert(C::kThreads == 64 + 32 * EW + 32, "block size of the configuration");
     static_assert(EW == 8 || (EW == 12 && NS == 1 && MODE == 2 && !GF32), "epilogue warps: 8, or 12 (2-SM BF16)");
     constexpr int kEpiWarps = C::kEpiWarps;
     constexpr int kEpiThreads = C::kEpiThreads;
@@ -1340,30 +1341,6 @@ void tiles_of(const DevMat& M, int i, std::vector<HostTile>* ph, bool cubic) {
             const int bn = std::min(kBN, M.Lp - b * kBN);
             ph[kApply].push_back(HostTile{TileTask{i, a, b, kApply}, (double)kBM * bn * M.sp});
         }
-}
-
-// Longest-processing-time assignment of an ordered tile list to `grid` CTAs;
-// each CTA keeps the list order (phase order), which the readiness waits
-// rely on for progress.
-void lpt_assign(const std::vector<HostTile>& order, int grid, std::vector<int>* off, std::vector<TileTask>* out) {
-    std::vector<std::vector<TileTask>> per(grid);
-    typedef std::pair<double, int> Load;
-    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
-    for (int c = 0; c < grid; ++c) pq.push(Load(0.0, c));
-    for (const HostTile& h : order) {
-        Load l = pq.top();
-        pq.pop();
-        per[l.second].push_back(h.t);
-        l.first += h.cost + 2.0e5;   // + per-tile fixed overhead
-        pq.push(l);
-    }
-    off->assign(grid + 1, 0);
-    out->clear();
-    for (int c = 0; c < grid; ++c) {
-        (*off)[c] = (int)out->size();
-        out->insert(out->end(), per[c].begin(), per[c].end());
-    }
-    (*off)[grid] = (int)out->size();
 }
 
 // Tile order inside a phase. Mode 0: longest first. Mode 1: by matrix
